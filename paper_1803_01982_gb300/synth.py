@@ -1,0 +1,97 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds none of the factorisation's arithmetic: it only builds test
+matrices with prescribed singular values (the paper's Type-1 recipe of
+Sec. 4.1 with the decays of the benchmark workloads), Kahan matrices (the
+classical failure case of greedy column pivoting mentioned in Sec. 2.1) and
+exactly low-rank matrices.  The Gaussian sketch Omega is NOT generated here:
+both the CUDA library and the oracle draw it themselves from the Philox
+counter stream.
+
+Recipes (every factor orthonormal = Q of a Householder QR of a seeded Gaussian
+matrix with diag(R) > 0, which makes Q unique):
+
+* ``decayed(m, n, sigma, noise, seed)``:  A = U_r diag(sigma) V_r^T + noise*E
+* ``kahan(n, c)``:                          Kahan's upper-triangular matrix
+* ``rank_k(m, n, k, seed)``:                X_L X_R^T with Gaussian factors
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def orthonormal(rng: np.random.Generator, m: int, r: int) -> np.ndarray:
+    G = rng.standard_normal((m, r))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def decayed(m: int, n: int, sigma, noise: float = 0.0, seed: int = 1,
+            dtype=np.float32) -> np.ndarray:
+    """A = U_r diag(sigma) V_r^T + noise * E, built in FP64, rounded once."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    r = sigma.shape[0]
+    rng = np.random.default_rng(seed)
+    U = orthonormal(rng, m, r)
+    V = orthonormal(rng, n, r)
+    A = (U * sigma[None, :]) @ V.T
+    if noise:
+        A += noise * rng.standard_normal((m, n))
+    return np.ascontiguousarray(A.astype(dtype))
+
+
+def decayed_torch(m: int, n: int, sigma, noise: float, seed: int, device: str = "cuda"):
+    """Same recipe as ``decayed`` for sizes too large for the host (20000^2):
+    built on the device with torch's seeded generator (input synthesis only,
+    not the factorisation path), FP64 then rounded once to FP32."""
+    import torch
+    sigma = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device)
+    r = sigma.shape[0]
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+
+    def orth(rows):
+        G = torch.randn(rows, r, generator=gen, device=device, dtype=torch.float64)
+        Q, R = torch.linalg.qr(G)
+        return Q * torch.sign(torch.diagonal(R))[None, :]
+
+    U = orth(m)
+    V = orth(n)
+    A = torch.empty(m, n, device=device, dtype=torch.float32)
+    rb = 2048
+    for i0 in range(0, m, rb):
+        i1 = min(m, i0 + rb)
+        blk = (U[i0:i1] * sigma[None, :]) @ V.T
+        if noise:
+            blk += noise * torch.randn(i1 - i0, n, generator=gen, device=device,
+                                       dtype=torch.float64)
+        A[i0:i1] = blk.to(torch.float32)
+    del U, V
+    return A
+
+
+def kahan(n: int, c: float = 0.285, dtype=np.float64) -> np.ndarray:
+    """Kahan matrix diag(1, s, ..., s^{n-1}) * (I - c * strict upper ones), s^2+c^2=1."""
+    s = np.sqrt(1.0 - c * c)
+    K = np.eye(n) - c * np.triu(np.ones((n, n)), 1)
+    K = (s ** np.arange(n))[:, None] * K
+    return np.ascontiguousarray(K.astype(dtype))
+
+
+def rank_k(m: int, n: int, k: int, seed: int = 3, dtype=np.float64) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray((rng.standard_normal((m, k)) @ rng.standard_normal((k, n)))
+                                .astype(dtype))
+
+
+def config1(dtype=np.float64) -> np.ndarray:
+    """1000 x 800, sigma_j = 0.9^j (j = 1..800), exactly that spectrum."""
+    return decayed(1000, 800, 0.9 ** np.arange(1, 801), 0.0, seed=1, dtype=dtype)
+
+
+def slow_decay(r: int) -> np.ndarray:
+    return np.arange(1, r + 1, dtype=np.float64) ** -1.5
+
+
+def fast_decay(r: int, base: float = 0.97) -> np.ndarray:
+    return base ** np.arange(1, r + 1, dtype=np.float64)
