@@ -1,0 +1,145 @@
+/*
+ * ffsrqr.h -- C ABI of the GB300 (sm_103a) Flip-Flop SRQR library.
+ *
+ * Flip-Flop Spectrum-Revealing QR (Feng, Xiao & Gu, arXiv 1803.01982,
+ * Alg. 9) computes a rank-k approximate SVD  A ~= U diag(S) V^T  of a dense
+ * m x n matrix:
+ *   sketch B = Omega A                       (Alg. 2, Omega ~ N(0,1)^{(k+p) x m})
+ *   partial QRCP of B for k steps -> Pi      (Alg. 1 on the sketch, Alg. 2)
+ *   QR of the pivoted panel A Pi(:,1:k)      (Alg. 2)
+ *   (R11 R12) = Q1^T A Pi                    (Eq. RRQR)
+ *   SRQR test / swaps on R11^{-1}R12 and the trailing norms (Alg. 4)
+ *   QR of (R11 R12)^T -> Qhat1              (Alg. 9, line 2)
+ *   tmp = A Pi Qhat1, svd(tmp) -> U, S, V    (Alg. 9, lines 3-5)
+ * All entry points take plain pointers and sizes; no C++ or framework types.
+ *
+ * Conventions
+ *   - Matrices are row-major.  A is m x n with leading dimension lda >= n.
+ *   - Device pointers are CUDA device addresses on the plan's device; host
+ *     pointers are ordinary (preferably pinned) host memory.
+ *   - Return codes: 0 = success; -i = argument i is invalid (LAPACK style);
+ *     positive codes are the FFSRQR_STATUS_* values below (numerical status,
+ *     reported through ffsrqr_info_t once the stream has been synchronised).
+ *   - Nothing here allocates device memory except where stated: the caller
+ *     owns A, the outputs and the workspace.
+ */
+#ifndef FFSRQR_H
+#define FFSRQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffsrqr_plan_s *ffsrqr_plan_t;
+
+/* Arithmetic modes (the precision layer).
+ *   FFSRQR_PLAIN_FP32: every product in FP32 on the CUDA cores (FFMA).
+ *   FFSRQR_MIXED:      the sketch B = Omega A on the tensor cores in TF32
+ *                      (one product; the sketch only chooses pivots), the two
+ *                      accuracy-bearing passes (Q1^T A and A Pi Qhat1) on the
+ *                      tensor cores as a three-product TF32 split that
+ *                      recovers FP32 accuracy; everything else FP32.
+ *   FFSRQR_FP64:       everything in FP64 on the CUDA cores (A, U, S, V are
+ *                      double). */
+#define FFSRQR_PLAIN_FP32 0
+#define FFSRQR_MIXED 1
+#define FFSRQR_FP64 3
+
+/* Numerical status codes (ffsrqr_info_t.status and positive return codes). */
+#define FFSRQR_STATUS_OK 0
+#define FFSRQR_STATUS_RANK_DEFICIENT 1 /* zero pivot norm / singular R11; results still written */
+#define FFSRQR_STATUS_SWAP_CAP 2       /* Alg. 4's swap loop hit max_swaps with g2 > g */
+#define FFSRQR_STATUS_TIMEOUT 3        /* a bounded device-side wait expired */
+#define FFSRQR_STATUS_NONFINITE 4      /* A contains Inf/NaN */
+#define FFSRQR_STATUS_WORKSPACE 5      /* workspace too small / admission refused */
+#define FFSRQR_STATUS_CUDA 6           /* a CUDA API call failed (see ffsrqr_last_cuda_error) */
+#define FFSRQR_STATUS_UNSUPPORTED 7    /* size outside what this build supports */
+
+/* Options (NULL -> defaults g = 2.0, max_swaps = 4k, flags = 0).
+ * g is the SRQR tolerance for g2 (Alg. 4, "a small number greater than one,
+ * like 2.0" in Sec. 2.2); max_swaps caps Alg. 4's while loop. */
+typedef struct {
+  double g;
+  int32_t max_swaps;
+  int32_t flags;
+} ffsrqr_opts_t;
+
+/* Per-run report, written by a device->host copy enqueued at the end of
+ * ffsrqr_run; valid after the stream has been synchronised.
+ *   g2_first / g2_final: g2 = |alpha| ||Rtilde^{-T}||_{1,2} (Eq. for g1, g2 in
+ *   Sec. 2.2) before and after the swap loop; cand_first: original index of the
+ *   first SRQR candidate column; alpha_first: its residual norm. */
+typedef struct {
+  int32_t status;
+  int32_t swaps;
+  double g2_first;
+  double g2_final;
+  int32_t cand_first;
+  int32_t jacobi_sweeps;
+  double alpha_first;
+} ffsrqr_info_t;
+
+/* Create a plan for m x n inputs, target rank k and oversampling p (the sketch
+ * has s = k + p rows; the paper's block size b = k and SRQR depth l = k).
+ * Requirements: 1 <= k <= n, k <= m, p >= 0, k + p <= m, k + p <= 256.
+ * mode is one of FFSRQR_*; opts may be NULL.  On success *workspace_bytes is
+ * the size of the device workspace ffsrqr_run needs (256-byte aligned).
+ * The plan holds only host metadata; it is bound to the current CUDA device.
+ * Errors: -1 plan NULL, -2 m, -3 n, -4 k, -5 p, -6 mode, -7 opts, -8
+ * workspace_bytes NULL; FFSRQR_STATUS_UNSUPPORTED for sizes this build does
+ * not handle; FFSRQR_STATUS_CUDA if the device query fails. */
+int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
+                const ffsrqr_opts_t *opts, size_t *workspace_bytes);
+
+/* Run Alg. 9 on A (device, m x n, row-major, lda >= n; FP32, or FP64 in
+ * FFSRQR_FP64 mode) and write
+ *   U   (device, m x k, row-major, ldu >= k),
+ *   S   (device, k, descending),
+ *   V   (device, n x k, row-major, ldv >= k),
+ *   piv (device, int32[n]): piv[0:k] = the final selected columns of A (0-based,
+ *        in R order); piv[k:n] = the remaining columns in ascending order.
+ * Omega is generated on the device from seed (Philox4x32-10, stream 0).
+ * workspace: device, >= the size reported by ffsrqr_plan, 256-byte aligned.
+ * stream: a cudaStream_t (NULL = legacy default stream).  The call only
+ * enqueues work; A is read-only.  info (may be NULL): host pointer, filled by
+ * an asynchronous copy (use pinned memory), valid after stream sync.
+ * Errors: -1 plan, -2 A, -3 lda, -5 U, -6 ldu, -7 S, -8 V, -9 ldv, -10 piv,
+ * -11 workspace; FFSRQR_STATUS_CUDA if a launch fails. */
+int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,
+               void *S, void *V, int64_t ldv, int32_t *piv, void *workspace, void *stream,
+               ffsrqr_info_t *info);
+
+/* Destroy a plan (host memory only).  Returns 0, or -1 for NULL. */
+int ffsrqr_destroy(ffsrqr_plan_t plan);
+
+/* Static description of a return / status code. */
+const char *ffsrqr_status_string(int code);
+
+/* Text of the last CUDA error seen by this library on the calling thread. */
+const char *ffsrqr_last_cuda_error(void);
+
+/* Location of an intermediate inside the workspace after ffsrqr_run, for
+ * step-by-step checks.  what: 0 Omega (s x m), 1 B^T (n x s), 2 S11 (k x k,
+ * R factor of the sketched pivot columns), 3 Q1 (m x k), 4 G^T = A^T Q1
+ * (n x k, original column order), 5 V' = Pi Qhat1 (n x k), 6 tmp = A V'
+ * (m x k), 7 trailing estimates r (n), 8 M_t (k x k, tmp = Q_t M_t).
+ * Writes the byte offset, row/column counts and leading dimension (elements)
+ * and the element size in bytes.  Returns 0 or -2 for an unknown item. */
+int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,
+                          int64_t *cols, int64_t *ld, int32_t *elem_bytes);
+
+/* Raw Philox4x32-10 blocks (Salmon et al., SC'11), the counter-based generator
+ * behind Omega (Alg. 2's Gaussian test matrix): for t < count, reads
+ * ctr_key[6t .. 6t+5] = (c0, c1, c2, c3, k0, k1) and writes the four output
+ * words to out[4t .. 4t+3].  Both pointers are device memory; the call only
+ * enqueues a kernel on stream.  Returns 0, -1/-2 for NULL pointers, -3 for
+ * count < 0, FFSRQR_STATUS_CUDA on launch failure. */
+int ffsrqr_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int32_t count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFSRQR_H */

@@ -1,0 +1,538 @@
+// dense_small.cuh -- the thin and k x k dense steps around the three passes:
+// gathers, row-wise triangular solves, Cholesky, the SRQR trailing-norm
+// estimate and g2 test (Alg. 4), the singular-vector sign rule and the pivot
+// output.  All kernels are templated on the working precision T.
+#pragma once
+
+#include "common.cuh"
+
+namespace ffq {
+
+// ---------------------------------------------------------------------------
+// Gathers
+// ---------------------------------------------------------------------------
+// P (m x ldp) = A(:, piv[0:k]); the pivoted panel of Alg. 2.
+template <typename T>
+__global__ void gather_cols_kernel(const T *__restrict__ A, int64_t lda, int64_t m, int k,
+                                   const int32_t *__restrict__ piv, T *__restrict__ P, int64_t ldp) {
+  const int64_t total = m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    const int j = (int)(e - i * k);
+    P[i * ldp + j] = A[i * lda + piv[j]];
+  }
+}
+
+// Dst (k x ldd) row l = Src row piv[l] (first `cols` entries).
+template <typename T>
+__global__ void gather_rows_kernel(const T *__restrict__ Src, int64_t lds, int k, int cols,
+                                   const int32_t *__restrict__ piv, T *__restrict__ Dst, int64_t ldd) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * cols; e += gridDim.x * blockDim.x) {
+    const int l = e / cols, t = e - l * cols;
+    Dst[(int64_t)l * ldd + t] = Src[(int64_t)piv[l] * lds + t];
+  }
+}
+
+// R11 (k x k) = upper triangle of G(:, J) where G^T = Gt (n x ldg):
+// R11(i, j) = Gt[piv[j], i] for i <= j.
+template <typename T>
+__global__ void extract_r11_kernel(const T *__restrict__ Gt, int64_t ldg, int k,
+                                   const int32_t *__restrict__ piv, T *__restrict__ R11) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    R11[e] = (i <= j) ? Gt[(int64_t)piv[j] * ldg + i] : T(0);
+  }
+}
+
+// Make the diagonal of an upper-triangular k x k matrix non-negative by
+// flipping rows (left multiplication by a sign matrix).
+template <typename T>
+__global__ void posdiag_rows_kernel(T *__restrict__ R, int k) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k;
+    if (R[(int64_t)i * k + i] < T(0)) R[e] = -R[e];
+  }
+}
+
+// Dst (rows x cols) = Src^T, Src (cols x rows) with leading dims.
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ Src, int64_t lds, int64_t rows, int64_t cols,
+                                 T *__restrict__ Dst, int64_t ldd) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t sr = c0 + yy, sc = r0 + threadIdx.x;  // Src row = dst col
+    tile[yy][threadIdx.x] = (sr < cols && sc < rows) ? Src[sr * lds + sc] : T(0);
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t dr = r0 + yy, dc = c0 + threadIdx.x;
+    if (dr < rows && dc < cols) Dst[dr * ldd + dc] = tile[threadIdx.x][yy];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row-wise triangular solve  Y P = X  (in place on X, M x k, leading dim ldx).
+// FWD: P upper triangular (forward substitution over columns 0..k-1).
+// !FWD: P lower triangular (backward substitution over columns k-1..0).
+// P(i, j) = Pm[i*psi + j*psj] (so P may be the transpose of a stored matrix).
+// Each row is solved independently by substitution, so each row's result is
+// backward stable: y (P + dP) = x with |dP| <= gamma_k |P|.
+// A warp solves R rows at a time; lane l owns columns l, l+32, ... (NS slots).
+// ---------------------------------------------------------------------------
+template <typename T, int NS, int R, bool FWD>
+__global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64_t ldx, int64_t M,
+                                                        int k, const T *__restrict__ Pm,
+                                                        int64_t psi, int64_t psj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ps = reinterpret_cast<T *>(smem_raw);  // k x k, row-major, P(j, c) at Ps[j*k + c]
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    Ps[e] = Pm[(int64_t)i * psi + (int64_t)j * psj];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t ngroups = (M + R - 1) / R;
+  for (int64_t grp = (int64_t)blockIdx.x * nwarp + wid; grp < ngroups;
+       grp += (int64_t)gridDim.x * nwarp) {
+    const int64_t r0 = grp * R;
+    T x[R][NS];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int c = lane + 32 * sl;
+        x[r][sl] = (r0 + r < M && c < k) ? X[(r0 + r) * ldx + c] : T(0);
+      }
+    if (FWD) {
+#pragma unroll
+      for (int jb = 0; jb < NS; ++jb) {
+        for (int ln = 0; ln < 32; ++ln) {
+          const int j = jb * 32 + ln;
+          if (j >= k) break;
+          const T d = Ps[j * k + j];
+          T yv[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) yv[r] = __shfl_sync(0xffffffffu, x[r][jb] / d, ln);
+          if (lane == ln) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r][jb] = yv[r];
+          }
+#pragma unroll
+          for (int sl = jb; sl < NS; ++sl) {
+            const int c = lane + 32 * sl;
+            const T pc = (c > j && c < k) ? Ps[j * k + c] : T(0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r][sl] = fma(-yv[r], pc, x[r][sl]);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int jb = NS - 1; jb >= 0; --jb) {
+        for (int ln = 31; ln >= 0; --ln) {
+          const int j = jb * 32 + ln;
+          if (j >= k) continue;
+          const T d = Ps[j * k + j];
+          T yv[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) yv[r] = __shfl_sync(0xffffffffu, x[r][jb] / d, ln);
+          if (lane == ln) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r][jb] = yv[r];
+          }
+#pragma unroll
+          for (int sl = 0; sl <= jb; ++sl) {
+            const int c = lane + 32 * sl;
+            const T pc = (c < j) ? Ps[j * k + c] : T(0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r][sl] = fma(-yv[r], pc, x[r][sl]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int c = lane + 32 * sl;
+        if (r0 + r < M && c < k) X[(r0 + r) * ldx + c] = x[r][sl];
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky  W = R^T R  (one block; W symmetric k x k, only its upper triangle
+// is read).  R is written upper triangular (k x k, zero below).  A non-positive
+// pivot marks the status RANK_DEFICIENT and continues with a unit pivot.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024) cholesky_kernel(const T *__restrict__ W, int k,
+                                                        T *__restrict__ R, int *ctl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);  // k x k
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) S[e] = W[e];
+  __syncthreads();
+  __shared__ T s_d;
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      T d = S[j * k + j];
+      if (!(d > T(0))) {
+        set_status(ctl, STATUS_RANK_DEFICIENT);
+        d = T(1);
+      }
+      s_d = sqrt(d);
+    }
+    __syncthreads();
+    const T d = s_d;
+    for (int c = j + threadIdx.x; c < k; c += blockDim.x) S[j * k + c] = (c == j) ? d : S[j * k + c] / d;
+    __syncthreads();
+    // trailing update of the upper triangle: S(i, c) -= R(j, i) R(j, c), j < i <= c
+    const int rem = k - j - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e / rem, c = j + 1 + e % rem;
+      if (c >= i) S[i * k + c] = fma(-S[j * k + i], S[j * k + c], S[i * k + c]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, c = e - i * k;
+    R[e] = (c >= i) ? S[e] : T(0);
+  }
+}
+
+// C (k x k) = A B for upper-triangular A, B (k x k) -- products of triangular
+// factors (R2 R1 in CholeskyQR2).
+template <typename T>
+__global__ void trmm_upper_kernel(const T *__restrict__ Am, const T *__restrict__ Bm, int k,
+                                  T *__restrict__ C) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    T acc = T(0);
+    for (int l = i; l <= j; ++l) acc = fma(Am[i * k + l], Bm[l * k + j], acc);
+    C[e] = (j >= i) ? acc : T(0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 4, trailing-norm estimate:  r_i = ||B(:,i) - B_J Z(:,i)||^2 / (k+p) for
+// columns i not in J, where Z = R11^{-1} G (so B - B_J Z is the sample
+// B2 - B1 R11^{-1} R12 of A(l+1:m, l+1:n)); CBt = (B_J Z)^T (n x lds).
+// Writes r (n; 0 for J) and a per-block argmax (value, index).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) trailing_norms_kernel(const T *__restrict__ Bt,
+                                                             const T *__restrict__ CBt, int64_t lds,
+                                                             int64_t n, int s, const int *__restrict__ sel,
+                                                             T *__restrict__ r, T *__restrict__ blk_v,
+                                                             int *__restrict__ blk_i) {
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  T bv = neg_inf<T>();
+  int bi = 0x7fffffff;
+  for (int64_t i = (int64_t)blockIdx.x * nwarp + wid; i < n; i += (int64_t)gridDim.x * nwarp) {
+    T acc = T(0);
+    for (int t = lane; t < s; t += 32) {
+      const T d = Bt[i * lds + t] - CBt[i * lds + t];
+      acc = fma(d, d, acc);
+    }
+    acc = warp_sum(acc) / T(s);
+    const bool inJ = sel[i] != 0;
+    if (lane == 0) r[i] = inJ ? T(0) : acc;
+    if (!inJ && better(acc, (int)i, bv, bi)) {
+      bv = acc;
+      bi = (int)i;
+    }
+  }
+  block_argmax(bv, bi, red_v, red_i);
+  if (threadIdx.x == 0) {
+    blk_v[blockIdx.x] = bv;
+    blk_i[blockIdx.x] = bi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SRQR one-step QR of the candidate column c (Alg. 4): z = A(:,c) - Q1 a with
+// a = G(:,c) = Q1^T A(:,c), then one re-orthogonalisation z -= Q1 (Q1^T z);
+// alpha = ||z||.  Three small kernels with block partial sums reduced in a
+// fixed order (deterministic).
+// ---------------------------------------------------------------------------
+// Final argmax over the per-block candidates -> ctl[CTL_CAND]; copies
+// a = Gt[c, :] into avec.
+template <typename T>
+__global__ void srqr_pick_kernel(const T *__restrict__ blk_v, const int *__restrict__ blk_i,
+                                 int nblk, const T *__restrict__ Gt, int64_t ldg, int k,
+                                 T *__restrict__ avec, int *ctl) {
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  T bv = neg_inf<T>();
+  int bi = 0x7fffffff;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    if (blk_i[b] != 0x7fffffff && better(blk_v[b], blk_i[b], bv, bi)) {
+      bv = blk_v[b];
+      bi = blk_i[b];
+    }
+  }
+  block_argmax(bv, bi, red_v, red_i);
+  if (threadIdx.x == 0) ctl[CTL_CAND] = bi;
+  if (bi == 0x7fffffff) return;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) avec[j] = Gt[(int64_t)bi * ldg + j];
+}
+
+// z_i = A(i, c) - sum_j Q1(i, j) a_j; partial h = Q1^T z per block (per-warp
+// partial rows summed in warp order, so the result does not depend on timing).
+template <typename T>
+__global__ void __launch_bounds__(256) srqr_resid_kernel(const T *__restrict__ A, int64_t lda,
+                                                         int64_t m, const T *__restrict__ Q1,
+                                                         int64_t ldq, int k, const T *__restrict__ avec,
+                                                         const int *ctl, T *__restrict__ z,
+                                                         T *__restrict__ hpart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nwarp = blockDim.x >> 5;
+  T *as = reinterpret_cast<T *>(smem_raw);  // k
+  T *hw = as + k;                           // nwarp x k
+  const int c = ctl[CTL_CAND];
+  if (c == 0x7fffffff) return;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) as[j] = avec[j];
+  for (int j = threadIdx.x; j < nwarp * k; j += blockDim.x) hw[j] = T(0);
+  __syncthreads();
+  const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * rows_per, i1 = min(m, i0 + rows_per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t i = i0 + wid; i < i1; i += nwarp) {
+    T acc = T(0);
+    for (int j = lane; j < k; j += 32) acc = fma(Q1[i * ldq + j], as[j], acc);
+    acc = warp_sum(acc);
+    const T zi = A[i * lda + c] - acc;
+    if (lane == 0) z[i] = zi;
+    for (int j = lane; j < k; j += 32) hw[wid * k + j] = fma(Q1[i * ldq + j], zi, hw[wid * k + j]);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    T acc = T(0);
+    for (int w = 0; w < nwarp; ++w) acc += hw[w * k + j];
+    hpart[(int64_t)blockIdx.x * k + j] = acc;
+  }
+}
+
+// z -= Q1 h (h = sum of block partials), partial ||z||^2 per block.
+template <typename T>
+__global__ void __launch_bounds__(256) srqr_reorth_kernel(int64_t m, const T *__restrict__ Q1,
+                                                          int64_t ldq, int k,
+                                                          const T *__restrict__ hpart, int nhp,
+                                                          const int *ctl, T *__restrict__ z,
+                                                          T *__restrict__ npart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *hs = reinterpret_cast<T *>(smem_raw);
+  __shared__ T red[32];
+  if (ctl[CTL_CAND] == 0x7fffffff) return;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    T acc = T(0);
+    for (int b = 0; b < nhp; ++b) acc += hpart[(int64_t)b * k + j];
+    hs[j] = acc;
+  }
+  __syncthreads();
+  const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * rows_per, i1 = min(m, i0 + rows_per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  T nacc = T(0);
+  for (int64_t i = i0 + wid; i < i1; i += nwarp) {
+    T acc = T(0);
+    for (int j = lane; j < k; j += 32) acc = fma(Q1[i * ldq + j], hs[j], acc);
+    acc = warp_sum(acc);
+    const T zi = z[i] - acc;
+    if (lane == 0) {
+      z[i] = zi;
+      nacc = fma(zi, zi, nacc);
+    }
+  }
+  nacc = block_sum(nacc, red);
+  if (threadIdx.x == 0) npart[blockIdx.x] = nacc;
+}
+
+// alpha = sqrt(sum npart); g2 = max(1, max_i sqrt(alpha^2 ||e_i^T R11^{-1}||^2 +
+// ((R11^{-1} a)_i)^2)) -- the closed form of |alpha| ||Rtilde^{-T}||_{1,2}
+// (Sec. 2.2); R11^{-1} a = Zt[c, :].  Rinv = R11^{-1} (k x k).
+template <typename T>
+__global__ void srqr_g2_kernel(const T *__restrict__ npart, int nnp, const T *__restrict__ Rinv,
+                               int k, const T *__restrict__ Zt, int64_t ldz, double g, int max_swaps,
+                               int *ctl, double *dctl, int first) {
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_alpha;
+  const int c = ctl[CTL_CAND];
+  if (c == 0x7fffffff) {
+    if (threadIdx.x == 0) {
+      dctl[D_G2] = 1.0;
+      if (first) dctl[D_G2_FIRST] = 1.0;
+      ctl[CTL_NEED_SWAP] = 0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    T acc = T(0);
+    for (int b = 0; b < nnp; ++b) acc += npart[b];
+    s_alpha = sqrt(acc);
+  }
+  __syncthreads();
+  const T alpha = s_alpha;
+  T bv = T(1);
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    T rn = T(0);
+    for (int j = i; j < k; ++j) rn = fma(Rinv[i * k + j], Rinv[i * k + j], rn);
+    const T u = Zt[(int64_t)c * ldz + i];
+    const T val = sqrt(alpha * alpha * rn + u * u);
+    if (better(val, i, bv, bi)) {
+      bv = val;
+      bi = i;
+    }
+  }
+  block_argmax(bv, bi, red_v, red_i);
+  if (threadIdx.x == 0) {
+    const double g2 = (double)bv;
+    dctl[D_G2] = g2;
+    dctl[D_ALPHA] = (double)alpha;
+    if (first) {
+      dctl[D_G2_FIRST] = g2;
+      dctl[D_ALPHA_FIRST] = (double)alpha;
+      ctl[CTL_CAND_FIRST] = c;
+    }
+    ctl[CTL_IMAX] = (bi == 0x7fffffff) ? -1 : bi;
+    const int need = (g2 > g) ? 1 : 0;
+    ctl[CTL_NEED_SWAP] = (need && ctl[CTL_SWAPS] < max_swaps) ? 1 : 0;
+    if (need && ctl[CTL_SWAPS] >= max_swaps) set_status(ctl, STATUS_SWAP_CAP);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Output helpers
+// ---------------------------------------------------------------------------
+// piv[k:n] = columns not in J, ascending (one block, chunked scan).
+__global__ void __launch_bounds__(1024) piv_rest_kernel(const int *__restrict__ sel, int64_t n, int k,
+                                                        int32_t *__restrict__ piv) {
+  __shared__ int counts[1024];
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t i0 = threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  int cnt = 0;
+  for (int64_t i = i0; i < i1; ++i) cnt += (sel[i] == 0);
+  counts[threadIdx.x] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int c = counts[t];
+      counts[t] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  int pos = k + counts[threadIdx.x];
+  for (int64_t i = i0; i < i1; ++i)
+    if (sel[i] == 0 && pos < n) piv[pos++] = (int32_t)i;
+}
+
+// Sign rule, stage 1: for each column j of U (m x k), the row of the
+// largest |U(i,j)| in each row chunk (ties -> lowest row).
+template <typename T>
+__global__ void __launch_bounds__(256) sign_partial_kernel(const T *__restrict__ U, int64_t ldu,
+                                                           int64_t m, int k, T *__restrict__ pv,
+                                                           int *__restrict__ pi) {
+  const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * rows_per, i1 = min(m, i0 + rows_per);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    T bv = T(-1);
+    int bi = 0x7fffffff;
+    for (int64_t i = i0; i < i1; ++i) {
+      const T a = fabs(U[i * ldu + j]);
+      if (a > bv) {
+        bv = a;
+        bi = (int)i;
+      }
+    }
+    pv[(int64_t)blockIdx.x * k + j] = bv;
+    pi[(int64_t)blockIdx.x * k + j] = bi;
+  }
+}
+
+// Stage 2: pick the winning row per column, sgn[j] = sign of U(row, j).
+template <typename T>
+__global__ void sign_final_kernel(const T *__restrict__ U, int64_t ldu, int k, const T *__restrict__ pv,
+                                  const int *__restrict__ pi, int nparts, T *__restrict__ sgn) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+    T bv = T(-1);
+    int bi = 0x7fffffff;
+    for (int b = 0; b < nparts; ++b) {
+      const T v = pv[(int64_t)b * k + j];
+      const int i = pi[(int64_t)b * k + j];
+      if (i != 0x7fffffff && (v > bv || (v == bv && i < bi))) {
+        bv = v;
+        bi = i;
+      }
+    }
+    sgn[j] = (bi != 0x7fffffff && U[(int64_t)bi * ldu + j] < T(0)) ? T(-1) : T(1);
+  }
+}
+
+// X(i, j) *= sgn[j]
+template <typename T>
+__global__ void scale_cols_kernel(T *__restrict__ X, int64_t ldx, int64_t rows, int k,
+                                  const T *__restrict__ sgn) {
+  const int64_t total = rows * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    const int j = (int)(e - i * k);
+    X[i * ldx + j] *= sgn[j];
+  }
+}
+
+// Copy a rows x cols block between leading dimensions.
+template <typename T>
+__global__ void copy2d_kernel(const T *__restrict__ Src, int64_t lds, T *__restrict__ Dst, int64_t ldd,
+                              int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    Dst[i * ldd + j] = Src[i * lds + j];
+  }
+}
+
+// Control-word defaults: g2 = 1 (no test possible when k = n), no candidate.
+__global__ void init_ctl_kernel(int *ctl, double *dctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    dctl[D_G2] = 1.0;
+    dctl[D_G2_FIRST] = 1.0;
+    ctl[CTL_CAND_FIRST] = -1;
+    ctl[CTL_CAND] = 0x7fffffff;
+  }
+}
+
+// Identity (k x k).
+template <typename T>
+__global__ void eye_kernel(T *__restrict__ X, int k) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
+    X[e] = ((e / k) == (e % k)) ? T(1) : T(0);
+}
+
+// Non-finite scan of A (sets status NONFINITE).
+template <typename T>
+__global__ void nonfinite_kernel(const T *__restrict__ A, int64_t lda, int64_t m, int64_t n, int *ctl) {
+  const int64_t total = m * n;
+  int bad = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    const T v = A[i * lda + j];
+    bad |= !(v - v == T(0));
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) {
+    atomicExch(ctl + CTL_NONFINITE, 1);
+    set_status(ctl, STATUS_NONFINITE);
+  }
+}
+
+}  // namespace ffq

@@ -1,0 +1,650 @@
+// ffsrqr.cu -- plan, workspace layout, pipeline and C ABI of the Flip-Flop SRQR
+// library (Feng, Xiao & Gu, arXiv 1803.01982, Alg. 9 with Alg. 4 and Alg. 2).
+//
+// Pipeline of ffsrqr_run (every step is a kernel of this library):
+//   a1  Omega = Philox/Box-Muller (s x m), s = k + p             (Alg. 2)
+//   a2  B^T = A^T Omega^T                                       pass 1 over A
+//   a3  partial QRCP of B, k steps -> piv[0:k], S11              (Alg. 1 on B)
+//   a4  panel A(:, J): Y = A_J S11^{-1}; CholeskyQR2(Y) -> Q1     (Alg. 2 QR)
+//   a5  G^T = A^T Q1  (= (R11 R12)^T, original column order)    pass 2 over A
+//   a6  R11 = triu(G(:, J)); Z^T = G^T R11^{-T}; trailing-norm estimate
+//       r_i = ||B(:,i) - B_J Z(:,i)||^2 / s; candidate c; alpha; g2  (Alg. 4)
+//   a7  swap loop while g2 > g (Alg. 4)                         [ffsrqr_swap.cuh]
+//   a8  V' = orth(Z^T) = Pi Qhat1 up to a k x k rotation         (Alg. 9, line 2)
+//   a9  tmp = A V'                                               pass 3 over A
+//   a10 Y_t = tmp (R11 R_z^T)^{-1}; CholeskyQR2(Y_t) -> Q_t, R_t;
+//       M_t = R_t R11 R_z^T (tmp = Q_t M_t); Jacobi SVD of M_t   (Alg. 9, line 4)
+//   a11 U = Q_t U_s, V = V' V_s, sign rule                       (Alg. 9, line 5)
+// The thin QR factorisations are preconditioned Cholesky-QR: each tall matrix
+// is first multiplied by the inverse of a triangular factor that makes it
+// well conditioned (the sketch's R factor S11 for the panel, R11 for G^T, and
+// R11 R_z^T for tmp), so two Cholesky-QR sweeps in FP32 give an orthonormal
+// basis of the same column space as Householder QR.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/ffsrqr.h"
+#include "common.cuh"
+#include "dense_small.cuh"
+#include "gemm_simt.cuh"
+#include "jacobi.cuh"
+#include "philox.cuh"
+#include "qrcp.cuh"
+
+using namespace ffq;
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+bool cuda_ok(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return true;
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  g_last_cuda_error = buf;
+  return false;
+}
+
+#define CK(call)                                    \
+  do {                                              \
+    if (!cuda_ok((call), #call)) return FFSRQR_STATUS_CUDA; \
+  } while (0)
+
+#define CKL(what)                                             \
+  do {                                                        \
+    if (!cuda_ok(cudaGetLastError(), what)) return FFSRQR_STATUS_CUDA; \
+  } while (0)
+
+struct Item {
+  size_t off = 0;
+  int64_t rows = 0, cols = 0, ld = 0;
+  int elem = 0;
+};
+
+}  // namespace
+
+struct ffsrqr_plan_s {
+  int64_t m, n;
+  int k, p, s, mode;
+  double g;
+  int max_swaps, flags;
+  int device, num_sms;
+  int elem;  // bytes per element of the working precision
+  int64_t ldm, ldn, lds, ldk;
+  // workspace items
+  size_t ws_bytes;
+  size_t off_ctl, off_dctl, off_info, off_om, off_bt, off_sel, off_s11, off_cval, off_cidx, off_ccol;
+  size_t off_q1, off_w, off_rc1, off_rc2, off_gt, off_r11, off_rinv, off_zt, off_bjt, off_cbt,
+      off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
+      off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_part, off_sgnv, off_sgni, off_sgn;
+  size_t part_cap;  // elements of the split-K buffer
+  int qrcp_grid, qrcp_threads;
+  size_t qrcp_smem;
+  int qrcp_cols, qrcp_spad;
+  int nblk_tn;  // blocks of the trailing-norm kernel
+  int nblk_res; // blocks of the SRQR residual kernels
+  int nblk_sign;
+  Item items[9];
+};
+
+namespace {
+
+constexpr long long kSpinLimit = 2000000;  // ~1 s of polling (each poll is an L2 round trip + 20 ns sleep)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+int launch_gemm(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int M, int N, int K,
+                const T *X, int64_t ldx, bool XM, const T *Y, int64_t ldy, bool YN, T *C,
+                int64_t ldc, T alpha = T(1), T beta = T(0)) {
+  if (M <= 0 || N <= 0) return 0;
+  T *part = reinterpret_cast<T *>(ws + P->off_part);
+  const bool wide = N > 64;
+  const int BM = 64, BN = wide ? 128 : 64;
+  const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
+  int splits = 1;
+  if (tiles < 2 * P->num_sms && K >= 512) {
+    splits = (int)cdiv(2 * P->num_sms, tiles);
+    splits = (int)std::min<int64_t>(splits, K / 256);
+    const int64_t cap = (int64_t)P->part_cap / ((int64_t)M * N);
+    splits = (int)std::min<int64_t>(splits, cap);
+    if (splits < 1) splits = 1;
+  }
+  const int klen = (int)round_up(cdiv(K, splits), 16);
+  splits = (int)cdiv(K, klen);
+  dim3 grid((unsigned)cdiv(M, BM), (unsigned)cdiv(N, BN), (unsigned)splits);
+#define GEMM_CASE(XMv, YNv)                                                                        \
+  if (XM == XMv && YN == YNv) {                                                                    \
+    if (wide)                                                                                      \
+      gemm_simt_kernel<T, 64, 128, 8, 4, 8, XMv, YNv>                                              \
+          <<<grid, 256, 0, st>>>(M, N, K, X, ldx, Y, ldy, C, ldc, klen, part, alpha, beta);        \
+    else                                                                                           \
+      gemm_simt_kernel<T, 64, 64, 16, 4, 4, XMv, YNv>                                              \
+          <<<grid, 256, 0, st>>>(M, N, K, X, ldx, Y, ldy, C, ldc, klen, part, alpha, beta);        \
+  }
+  GEMM_CASE(true, true)
+  GEMM_CASE(true, false)
+  GEMM_CASE(false, true)
+  GEMM_CASE(false, false)
+#undef GEMM_CASE
+  CKL("gemm_simt");
+  if (splits > 1) {
+    const int64_t total = (int64_t)M * N;
+    splitk_reduce_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(total, 256), 4 * P->num_sms), 256, 0, st>>>(
+        M, N, splits, part, C, ldc, alpha, beta);
+    CKL("splitk_reduce");
+  }
+  return 0;
+}
+
+template <typename T, bool FWD>
+int launch_trsm(cudaStream_t st, const ffsrqr_plan_s *P, T *X, int64_t ldx, int64_t M, const T *Pm,
+                int64_t psi, int64_t psj) {
+  const int k = P->k;
+  const size_t smem = (size_t)k * k * sizeof(T);
+  const int threads = 512;
+  const int64_t groups = cdiv(M, 4);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(groups, threads / 32), P->num_sms));
+  const int ns = (int)cdiv(k, 32);
+#define TRSM_CASE(NSv)                                                                        \
+  if (ns <= NSv) {                                                                            \
+    auto fn = trsm_rows_kernel<T, NSv, 4, FWD>;                                               \
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
+    fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj);                              \
+    CKL("trsm_rows");                                                                         \
+    return 0;                                                                                 \
+  }
+  TRSM_CASE(1)
+  TRSM_CASE(2)
+  TRSM_CASE(4)
+  TRSM_CASE(7)
+#undef TRSM_CASE
+  return FFSRQR_STATUS_UNSUPPORTED;
+}
+
+template <typename T>
+int launch_chol(cudaStream_t st, const ffsrqr_plan_s *P, const T *W, T *R, int *ctl) {
+  const int k = P->k;
+  const size_t smem = (size_t)k * k * sizeof(T);
+  CK(cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cholesky_kernel<T><<<1, 1024, smem, st>>>(W, k, R, ctl);
+  CKL("cholesky");
+  return 0;
+}
+
+// CholeskyQR2 on X (M x k, ldx) in place: X <- orthonormal Q, Rout = R2 R1.
+template <typename T>
+int cholqr2(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, T *X, int64_t ldx, int64_t M,
+            T *Rout) {
+  const int k = P->k;
+  T *W = reinterpret_cast<T *>(ws + P->off_w);
+  T *R1 = reinterpret_cast<T *>(ws + P->off_rc1);
+  T *R2 = reinterpret_cast<T *>(ws + P->off_rc2);
+  int *ctl = reinterpret_cast<int *>(ws + P->off_ctl);
+  int rc;
+  if ((rc = launch_gemm<T>(st, P, ws, k, k, (int)M, X, ldx, true, X, ldx, true, W, k))) return rc;
+  if ((rc = launch_chol<T>(st, P, W, R1, ctl))) return rc;
+  if ((rc = launch_trsm<T, true>(st, P, X, ldx, M, R1, k, 1))) return rc;
+  if ((rc = launch_gemm<T>(st, P, ws, k, k, (int)M, X, ldx, true, X, ldx, true, W, k))) return rc;
+  if ((rc = launch_chol<T>(st, P, W, R2, ctl))) return rc;
+  if ((rc = launch_trsm<T, true>(st, P, X, ldx, M, R2, k, 1))) return rc;
+  if (Rout) {
+    trmm_upper_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(R2, R1, k, Rout);
+    CKL("trmm_upper");
+  }
+  return 0;
+}
+
+template <typename T>
+struct WsPtrs {
+  int *ctl;
+  double *dctl;
+  T *om, *bt, *s11, *cval, *ccol, *q1, *gt, *r11, *rinv, *zt, *bjt, *cbt, *r, *bv, *avec, *z, *hpart,
+      *npart, *vp, *rz, *tmp, *yt, *rt, *t1, *mt, *us, *vs, *sgnv, *sgn;
+  int *sel, *cidx, *bi, *sgni;
+};
+
+template <typename T>
+WsPtrs<T> ws_ptrs(const ffsrqr_plan_s *P, unsigned char *ws) {
+  WsPtrs<T> w;
+#define PT(name, off) w.name = reinterpret_cast<decltype(w.name)>(ws + P->off)
+  PT(ctl, off_ctl);
+  PT(dctl, off_dctl);
+  PT(om, off_om);
+  PT(bt, off_bt);
+  PT(s11, off_s11);
+  PT(cval, off_cval);
+  PT(ccol, off_ccol);
+  PT(q1, off_q1);
+  PT(gt, off_gt);
+  PT(r11, off_r11);
+  PT(rinv, off_rinv);
+  PT(zt, off_zt);
+  PT(bjt, off_bjt);
+  PT(cbt, off_cbt);
+  PT(r, off_r);
+  PT(bv, off_bv);
+  PT(avec, off_avec);
+  PT(z, off_z);
+  PT(hpart, off_hpart);
+  PT(npart, off_npart);
+  PT(vp, off_vp);
+  PT(rz, off_rz);
+  PT(tmp, off_tmp);
+  PT(yt, off_yt);
+  PT(rt, off_rt);
+  PT(t1, off_t1);
+  PT(mt, off_mt);
+  PT(us, off_us);
+  PT(vs, off_vs);
+  PT(sgnv, off_sgnv);
+  PT(sgn, off_sgn);
+  PT(sel, off_sel);
+  PT(cidx, off_cidx);
+  PT(bi, off_bi);
+  PT(sgni, off_sgni);
+#undef PT
+  return w;
+}
+
+__global__ void info_kernel(const int *ctl, const double *dctl, ffsrqr_info_t *info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  info->status = ctl[CTL_STATUS];
+  info->swaps = ctl[CTL_SWAPS];
+  info->g2_first = dctl[D_G2_FIRST];
+  info->g2_final = dctl[D_G2];
+  info->cand_first = ctl[CTL_CAND_FIRST];
+  info->jacobi_sweeps = ctl[CTL_JACOBI_SWEEPS];
+  info->alpha_first = dctl[D_ALPHA_FIRST];
+}
+
+// SRQR test on the current candidate (Alg. 4): pick c from the trailing
+// estimates, one-step QR residual alpha, closed-form g2.
+template <typename T>
+int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A, int64_t lda,
+              int first) {
+  const int k = P->k;
+  srqr_pick_kernel<T><<<1, 256, 0, st>>>(w.bv, w.bi, P->nblk_tn, w.gt, P->ldk, k, w.avec, w.ctl);
+  CKL("srqr_pick");
+  const int threads = 256;
+  const size_t smem1 = (size_t)(k + (threads / 32) * k) * sizeof(T);
+  srqr_resid_kernel<T><<<P->nblk_res, threads, smem1, st>>>(A, lda, P->m, w.q1, P->ldk, k, w.avec,
+                                                            w.ctl, w.z, w.hpart);
+  CKL("srqr_resid");
+  srqr_reorth_kernel<T><<<P->nblk_res, threads, (size_t)k * sizeof(T), st>>>(
+      P->m, w.q1, P->ldk, k, w.hpart, P->nblk_res, w.ctl, w.z, w.npart);
+  CKL("srqr_reorth");
+  srqr_g2_kernel<T><<<1, 256, 0, st>>>(w.npart, P->nblk_res, w.rinv, k, w.zt, P->ldk, P->g,
+                                       P->max_swaps, w.ctl, w.dctl, first);
+  CKL("srqr_g2");
+  return 0;
+}
+
+template <typename T>
+int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
+             int64_t ldv, int32_t *piv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
+  const int64_t m = P->m, n = P->n;
+  const int k = P->k, s = P->s;
+  const int64_t ldm = P->ldm, lds = P->lds, ldk = P->ldk;
+  WsPtrs<T> w = ws_ptrs<T>(P, ws);
+  const int nsm = P->num_sms;
+  int rc;
+
+  CK(cudaMemsetAsync(ws + P->off_ctl, 0, CTL_WORDS * sizeof(int), st));
+  CK(cudaMemsetAsync(ws + P->off_dctl, 0, D_WORDS * sizeof(double), st));
+  CK(cudaMemsetAsync(w.sel, 0, (size_t)n * sizeof(int), st));
+  CK(cudaMemsetAsync(piv, 0, (size_t)n * sizeof(int32_t), st));
+  init_ctl_kernel<<<1, 32, 0, st>>>(w.ctl, w.dctl);
+  CKL("init_ctl");
+  if (P->flags & 1) {
+    nonfinite_kernel<T><<<4 * nsm, 256, 0, st>>>(A, lda, m, n, w.ctl);
+    CKL("nonfinite");
+  }
+
+  // a1: Omega
+  {
+    const int64_t nq = cdiv((int64_t)s * m, 4);
+    omega_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(nq, 256), 8 * nsm), 256, 0, st>>>(w.om, s, m, ldm,
+                                                                                         seed);
+    CKL("omega");
+  }
+  // a2: pass 1, B^T (n x s) = A^T Omega^T
+  if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, (int)m, A, lda, true, w.om, ldm, false, w.bt, lds)))
+    return rc;
+  // a3: QRCP on the sketch
+  {
+    QrcpArgs<T> qa;
+    qa.Bt = w.bt;
+    qa.n = n;
+    qa.s = s;
+    qa.lds = (int)lds;
+    qa.k = k;
+    qa.piv = piv;
+    qa.S11 = w.s11;
+    qa.cand_val = w.cval;
+    qa.cand_idx = w.cidx;
+    qa.cand_col = w.ccol;
+    qa.sel = w.sel;
+    qa.ctl = w.ctl;
+    qa.spin_limit = kSpinLimit;
+    qa.cols_per_block = P->qrcp_cols;
+    qa.s_pad = P->qrcp_spad;
+    void *args[] = {&qa};
+    CK(cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)P->qrcp_smem));
+    CK(cudaLaunchCooperativeKernel((void *)qrcp_kernel<T>, dim3(P->qrcp_grid), dim3(P->qrcp_threads),
+                                   args, P->qrcp_smem, st));
+  }
+  posdiag_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.s11, k);
+  CKL("posdiag");
+  // a4: panel Y = A_J S11^{-1}, CholeskyQR2 -> Q1
+  gather_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(
+      A, lda, m, k, piv, w.q1, ldk);
+  CKL("gather_cols");
+  if ((rc = launch_trsm<T, true>(st, P, w.q1, ldk, m, w.s11, k, 1))) return rc;
+  if ((rc = cholqr2<T>(st, P, ws, w.q1, ldk, m, nullptr))) return rc;
+  // a5: pass 2, G^T (n x k) = A^T Q1
+  if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, (int)m, A, lda, true, w.q1, ldk, true, w.gt, ldk)))
+    return rc;
+  // a6: R11, R11^{-1}, Z^T = G^T R11^{-T}
+  extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11);
+  CKL("extract_r11");
+  eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k);
+  CKL("eye");
+  if ((rc = launch_trsm<T, true>(st, P, w.rinv, k, k, w.r11, k, 1))) return rc;
+  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, w.zt,
+                                                                                          ldk, n, k);
+  CKL("copy_zt");
+  if ((rc = launch_trsm<T, false>(st, P, w.zt, ldk, n, w.r11, 1, k))) return rc;
+  // trailing-norm estimate and the first SRQR test
+  gather_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * s, 256), 256, 0, st>>>(w.bt, lds, k, s, piv, w.bjt,
+                                                                             lds);
+  CKL("gather_rows");
+  if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, k, w.zt, ldk, false, w.bjt, lds, true, w.cbt, lds)))
+    return rc;
+  trailing_norms_kernel<T><<<P->nblk_tn, 256, 0, st>>>(w.bt, w.cbt, lds, n, s, w.sel, w.r, w.bv, w.bi);
+  CKL("trailing_norms");
+  if (k < n) {
+    if ((rc = srqr_test<T>(st, P, w, A, lda, 1))) return rc;
+  }
+  // a8: V' = orth(Z^T), R_z
+  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.zt, ldk, w.vp,
+                                                                                          ldk, n, k);
+  CKL("copy_vp");
+  if ((rc = cholqr2<T>(st, P, ws, w.vp, ldk, n, w.rz))) return rc;
+  // a9: pass 3, tmp (m x k) = A V'
+  if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, (int)n, A, lda, false, w.vp, ldk, true, w.tmp, ldk)))
+    return rc;
+  // a10: Y_t = tmp R_z^{-T} R11^{-1}; CholeskyQR2 -> Q_t, R_t; M_t = R_t R11 R_z^T
+  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(w.tmp, ldk, w.yt,
+                                                                                          ldk, m, k);
+  CKL("copy_yt");
+  if ((rc = launch_trsm<T, false>(st, P, w.yt, ldk, m, w.rz, 1, k))) return rc;
+  if ((rc = launch_trsm<T, true>(st, P, w.yt, ldk, m, w.r11, k, 1))) return rc;
+  if ((rc = cholqr2<T>(st, P, ws, w.yt, ldk, m, w.rt))) return rc;
+  if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.rt, k, false, w.r11, k, true, w.t1, k))) return rc;
+  if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.t1, k, false, w.rz, k, false, w.mt, k))) return rc;
+  {
+    const int kk = k + (k & 1);
+    const size_t smem = (size_t)kk * k * sizeof(T) + (size_t)(2 * kk + kk) * sizeof(T) +
+                        (size_t)(kk + 4) * sizeof(int) + 64;
+    CK(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const T eps = (sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16);
+    const T tol = (sizeof(T) == 4) ? T(4) * sqrt(T(k)) * eps : T(k) * eps;
+    jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, w.ctl, 40, tol);
+    CKL("jacobi_svd");
+  }
+  // a11: U = Q_t U_s, V = V' V_s, sign rule
+  if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, k, w.yt, ldk, false, w.us, k, true, U, ldu))) return rc;
+  if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, k, w.vp, ldk, false, w.vs, k, true, V, ldv))) return rc;
+  sign_partial_kernel<T><<<P->nblk_sign, 256, 0, st>>>(U, ldu, m, k, w.sgnv, w.sgni);
+  CKL("sign_partial");
+  sign_final_kernel<T><<<(unsigned)cdiv(k, 256), 256, 0, st>>>(U, ldu, k, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
+  CKL("sign_final");
+  scale_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(U, ldu, m, k,
+                                                                                              w.sgn);
+  scale_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(V, ldv, n, k,
+                                                                                              w.sgn);
+  CKL("scale_cols");
+  piv_rest_kernel<<<1, 1024, 0, st>>>(w.sel, n, k, piv);
+  CKL("piv_rest");
+  ffsrqr_info_t *dinfo = reinterpret_cast<ffsrqr_info_t *>(ws + P->off_info);
+  info_kernel<<<1, 32, 0, st>>>(w.ctl, w.dctl, dinfo);
+  CKL("info");
+  if (info) CK(cudaMemcpyAsync(info, dinfo, sizeof(ffsrqr_info_t), cudaMemcpyDeviceToHost, st));
+  return 0;
+}
+
+template <typename T>
+void layout(ffsrqr_plan_s *P) {
+  const int64_t m = P->m, n = P->n;
+  const int k = P->k, s = P->s;
+  const int64_t ldm = P->ldm, lds = P->lds, ldk = P->ldk;
+  const int nsm = P->num_sms;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t E = sizeof(T);
+  P->off_ctl = take(CTL_WORDS * sizeof(int));
+  P->off_dctl = take(D_WORDS * sizeof(double));
+  P->off_info = take(sizeof(ffsrqr_info_t));
+  P->off_om = take((size_t)s * ldm * E);
+  P->off_bt = take((size_t)n * lds * E);
+  P->off_sel = take((size_t)n * sizeof(int));
+  P->off_s11 = take((size_t)k * k * E);
+  P->off_cval = take((size_t)2 * P->qrcp_grid * E);
+  P->off_cidx = take((size_t)2 * P->qrcp_grid * sizeof(int));
+  P->off_ccol = take((size_t)2 * P->qrcp_grid * lds * E);
+  P->off_q1 = take((size_t)m * ldk * E);
+  P->off_w = take((size_t)k * k * E);
+  P->off_rc1 = take((size_t)k * k * E);
+  P->off_rc2 = take((size_t)k * k * E);
+  P->off_gt = take((size_t)n * ldk * E);
+  P->off_r11 = take((size_t)k * k * E);
+  P->off_rinv = take((size_t)k * k * E);
+  P->off_zt = take((size_t)n * ldk * E);
+  P->off_bjt = take((size_t)k * lds * E);
+  P->off_cbt = take((size_t)n * lds * E);
+  P->off_r = take((size_t)n * E);
+  P->nblk_tn = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 8), 2 * nsm));
+  P->off_bv = take((size_t)P->nblk_tn * E);
+  P->off_bi = take((size_t)P->nblk_tn * sizeof(int));
+  P->off_avec = take((size_t)k * E);
+  P->off_z = take((size_t)m * E);
+  P->nblk_res = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 64), nsm));
+  P->off_hpart = take((size_t)P->nblk_res * k * E);
+  P->off_npart = take((size_t)P->nblk_res * E);
+  P->off_vp = take((size_t)n * ldk * E);
+  P->off_rz = take((size_t)k * k * E);
+  P->off_tmp = take((size_t)m * ldk * E);
+  P->off_yt = take((size_t)m * ldk * E);
+  P->off_rt = take((size_t)k * k * E);
+  P->off_t1 = take((size_t)k * k * E);
+  P->off_mt = take((size_t)k * k * E);
+  P->off_us = take((size_t)k * k * E);
+  P->off_vs = take((size_t)k * k * E);
+  P->nblk_sign = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max(m, n), 64), nsm));
+  P->off_sgnv = take((size_t)P->nblk_sign * k * E);
+  P->off_sgni = take((size_t)P->nblk_sign * k * sizeof(int));
+  P->off_sgn = take((size_t)k * E);
+  P->part_cap = (size_t)std::max<int64_t>((int64_t)k * k * 64, (int64_t)4 * 1024 * 1024 / E);
+  P->off_part = take(P->part_cap * E);
+  P->ws_bytes = off;
+  auto item = [&](int i, size_t o, int64_t r, int64_t c, int64_t ld) {
+    P->items[i].off = o;
+    P->items[i].rows = r;
+    P->items[i].cols = c;
+    P->items[i].ld = ld;
+    P->items[i].elem = (int)E;
+  };
+  item(0, P->off_om, s, m, ldm);
+  item(1, P->off_bt, n, s, lds);
+  item(2, P->off_s11, k, k, k);
+  item(3, P->off_q1, m, k, ldk);
+  item(4, P->off_gt, n, k, ldk);
+  item(5, P->off_vp, n, k, ldk);
+  item(6, P->off_tmp, m, k, ldk);
+  item(7, P->off_r, n, 1, 1);
+  item(8, P->off_mt, k, k, k);
+}
+
+template <typename T>
+int plan_qrcp(ffsrqr_plan_s *P) {
+  const int s = P->s;
+  P->qrcp_threads = 512;
+  P->qrcp_spad = (int)round_up(s, 4);
+  int dev_smem = 0;
+  CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+  const size_t budget = (size_t)dev_smem - 2048;
+  // slab width per block so that the slab fits; at least 16 columns per block
+  int64_t grid = std::min<int64_t>(P->num_sms, std::max<int64_t>(1, cdiv(P->n, 16)));
+  for (;;) {
+    const int64_t cols = cdiv(P->n, grid);
+    const size_t need = ((size_t)cols * P->qrcp_spad + cols + P->qrcp_spad) * sizeof(T);
+    if (need <= budget) {
+      P->qrcp_cols = (int)cols;
+      P->qrcp_smem = need;
+      break;
+    }
+    if (grid >= P->num_sms) return FFSRQR_STATUS_UNSUPPORTED;  // sketch too large for on-chip slabs
+    grid = std::min<int64_t>(P->num_sms, grid * 2);
+  }
+  int per_sm = 0;
+  CK(cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->qrcp_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel<T>, P->qrcp_threads, P->qrcp_smem));
+  if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
+  P->qrcp_grid = (int)grid;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
+                const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (m < 1 || m > (int64_t)INT32_MAX) return -2;
+  if (n < 1 || n > (int64_t)INT32_MAX) return -3;
+  if (k < 1 || k > n || k > m) return -4;
+  if (p < 0 || (int64_t)k + p > m || k + p > 256) return -5;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -6;
+  if (opts && !(opts->g > 1.0)) return -7;
+  if (opts && opts->max_swaps < 0) return -7;
+  if (!workspace_bytes) return -8;
+  const int elem = (mode == FFSRQR_FP64) ? 8 : 4;
+  if ((size_t)k * k * elem > 200 * 1024) return FFSRQR_STATUS_UNSUPPORTED;
+  ffsrqr_plan_s *P = new (std::nothrow) ffsrqr_plan_s();
+  if (!P) return FFSRQR_STATUS_WORKSPACE;
+  P->m = m;
+  P->n = n;
+  P->k = k;
+  P->p = p;
+  P->s = k + p;
+  P->mode = mode;
+  P->g = opts ? opts->g : 2.0;
+  P->max_swaps = opts ? opts->max_swaps : 4 * k;
+  P->flags = opts ? opts->flags : 0;
+  P->elem = elem;
+  P->ldm = round_up(m, 4);
+  P->ldn = round_up(n, 4);
+  P->lds = round_up(P->s, 4);
+  P->ldk = round_up(k, 4);
+  if (!cuda_ok(cudaGetDevice(&P->device), "cudaGetDevice") ||
+      !cuda_ok(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device),
+               "cudaDeviceGetAttribute")) {
+    delete P;
+    return FFSRQR_STATUS_CUDA;
+  }
+  int rc = (elem == 8) ? plan_qrcp<double>(P) : plan_qrcp<float>(P);
+  if (rc) {
+    delete P;
+    return rc;
+  }
+  if (elem == 8) layout<double>(P);
+  else layout<float>(P);
+  *workspace_bytes = P->ws_bytes;
+  *plan = P;
+  return 0;
+}
+
+int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,
+               void *S, void *V, int64_t ldv, int32_t *piv, void *workspace, void *stream,
+               ffsrqr_info_t *info) {
+  if (!plan) return -1;
+  if (!A) return -2;
+  if (lda < plan->n) return -3;
+  if (!U) return -5;
+  if (ldu < plan->k) return -6;
+  if (!S) return -7;
+  if (!V) return -8;
+  if (ldv < plan->k) return -9;
+  if (!piv) return -10;
+  if (!workspace || ((uintptr_t)workspace & 255u)) return -11;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
+  if (plan->elem == 8)
+    return run_impl<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S,
+                            (double *)V, ldv, piv, ws, st, info);
+  return run_impl<float>(plan, (const float *)A, lda, seed, (float *)U, ldu, (float *)S, (float *)V,
+                         ldv, piv, ws, st, info);
+}
+
+int ffsrqr_destroy(ffsrqr_plan_t plan) {
+  if (!plan) return -1;
+  delete plan;
+  return 0;
+}
+
+const char *ffsrqr_status_string(int code) {
+  switch (code) {
+    case 0: return "ok";
+    case FFSRQR_STATUS_RANK_DEFICIENT: return "rank deficient (zero pivot norm or singular factor)";
+    case FFSRQR_STATUS_SWAP_CAP: return "SRQR swap cap reached with g2 > g";
+    case FFSRQR_STATUS_TIMEOUT: return "bounded device wait expired";
+    case FFSRQR_STATUS_NONFINITE: return "input contains Inf or NaN";
+    case FFSRQR_STATUS_WORKSPACE: return "workspace too small or admission refused";
+    case FFSRQR_STATUS_CUDA: return "CUDA API error";
+    case FFSRQR_STATUS_UNSUPPORTED: return "size not supported by this build";
+    default: break;
+  }
+  if (code < 0) return "invalid argument";
+  return "unknown status";
+}
+
+const char *ffsrqr_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,
+                          int64_t *cols, int64_t *ld, int32_t *elem_bytes) {
+  if (!plan) return -1;
+  if (what < 0 || what > 8) return -2;
+  const Item &it = plan->items[what];
+  if (offset) *offset = it.off;
+  if (rows) *rows = it.rows;
+  if (cols) *cols = it.cols;
+  if (ld) *ld = it.ld;
+  if (elem_bytes) *elem_bytes = it.elem;
+  return 0;
+}
+
+int ffsrqr_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int32_t count, void *stream) {
+  if (!ctr_key) return -1;
+  if (!out) return -2;
+  if (count < 0) return -3;
+  if (count == 0) return 0;
+  philox_raw_kernel<<<(unsigned)cdiv(count, 128), 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      ctr_key, out, count);
+  CKL("philox_raw");
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// qrcp.cuh -- partial QR with column pivoting of the sketch B (Alg. 1 applied to
+// the (b+p) x n sample of Alg. 2, b = k), as one persistent cooperative kernel.
+//
+// Layout: Bt = B^T (n x lds, column i of B is the contiguous row i of Bt).  The
+// n columns are split into contiguous slabs, one per block; each block keeps
+// its slab of B resident in shared memory for all k steps, together with the
+// exact trailing squared norms ||B(j:s, i)||^2 of its columns.
+//
+// Step j (one bounded grid barrier per step):
+//   1. every block publishes its best unselected column (largest trailing norm,
+//      ties to the lowest original index) and a copy of that column;
+//   2. barrier;
+//   3. every block reduces the published candidates to the same winner p,
+//      loads the winner's column and forms the Householder reflector
+//      H = I - tau v v^T from B(j:s, p) (beta = -sign(x_j) ||x||);
+//   4. each block applies H to its own unselected columns and recomputes their
+//      trailing norms ||B(j+1:s, i)||^2 exactly (no downdating).
+// Outputs: piv[0:k] (original indices, in pivot order), S11 (k x k, row-major,
+// the R factor of the pivoted sketch columns: S11(0:j, j) = transformed pivot
+// column above the diagonal, S11(j, j) = beta), status RANK_DEFICIENT if a
+// winner has zero trailing norm.
+#pragma once
+
+#include "common.cuh"
+
+namespace ffq {
+
+template <typename T>
+struct QrcpArgs {
+  const T *Bt;
+  int64_t n;
+  int s, lds, k;
+  int32_t *piv;
+  T *S11;            // k x k
+  T *cand_val;       // [2][G]
+  int *cand_idx;     // [2][G]
+  T *cand_col;       // [2][G][lds]
+  int *sel;          // [n] 1 if selected (written for downstream kernels)
+  int *ctl;
+  long long spin_limit;
+  int cols_per_block;  // slab width (columns)
+  int s_pad;           // slab column stride in shared memory
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *slab = reinterpret_cast<T *>(smem_raw);                        // [cols][s_pad]
+  T *nrm = slab + (size_t)a.cols_per_block * a.s_pad;               // [cols]
+  T *v = nrm + a.cols_per_block;                                    // [s_pad]
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_tau, s_beta;
+  __shared__ int s_win_blk, s_win_col;
+
+  const int G = gridDim.x, b = blockIdx.x;
+  const int64_t c0 = (a.n * b) / G, c1 = (a.n * (b + 1)) / G;
+  const int ncol = (int)(c1 - c0);
+  const int s = a.s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  unsigned *bar = reinterpret_cast<unsigned *>(a.ctl + CTL_BARRIER0);
+
+  // load slab, initial norms
+  for (int c = wid; c < ncol; c += nwarp) {
+    T acc = T(0);
+    for (int t = lane; t < s; t += 32) {
+      const T x = a.Bt[(c0 + c) * a.lds + t];
+      slab[(size_t)c * a.s_pad + t] = x;
+      acc += x * x;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) nrm[c] = acc;
+  }
+  __syncthreads();
+
+  for (int j = 0; j < a.k; ++j) {
+    const int buf = j & 1;
+    // 1. local candidate
+    T bv = neg_inf<T>();
+    int bi = 0x7fffffff;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+      const T x = nrm[c];
+      if (x >= T(0) && better(x, (int)(c0 + c), bv, bi)) {
+        bv = x;
+        bi = (int)(c0 + c);
+      }
+    }
+    block_argmax(bv, bi, red_v, red_i);
+    if (threadIdx.x == 0) {
+      a.cand_val[buf * G + b] = bv;
+      a.cand_idx[buf * G + b] = bi;
+    }
+    if (bi != 0x7fffffff) {
+      const int lc = (int)(bi - c0);
+      for (int t = threadIdx.x; t < s; t += blockDim.x)
+        a.cand_col[((size_t)buf * G + b) * a.lds + t] = slab[(size_t)lc * a.s_pad + t];
+    }
+    // 2. barrier
+    if (!grid_barrier(bar, (unsigned)((j + 1) * G), a.ctl, a.spin_limit)) return;
+    // 3. winner, reflector
+    {
+      T wv = neg_inf<T>();
+      int wi = 0x7fffffff, wb = -1;
+      for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const T x = a.cand_val[buf * G + g];
+        const int ix = a.cand_idx[buf * G + g];
+        if (ix != 0x7fffffff && better(x, ix, wv, wi)) {
+          wv = x;
+          wi = ix;
+        }
+      }
+      block_argmax(wv, wi, red_v, red_i);
+      if (threadIdx.x == 0 && wi == 0x7fffffff) {
+        // no finite candidate left (NaN input): record and skip this step
+        s_win_blk = -1;
+        s_win_col = -1;
+        set_status(a.ctl, STATUS_NONFINITE);
+      } else if (threadIdx.x == 0) {
+        // which block owns column wi
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if ((a.n * mid) / G <= wi) lo = mid;
+          else hi = mid - 1;
+        }
+        wb = lo;
+        s_win_blk = wb;
+        s_win_col = wi;
+        if (!(wv > T(0))) set_status(a.ctl, STATUS_RANK_DEFICIENT);
+      }
+      __syncthreads();
+      wb = s_win_blk;
+      wi = s_win_col;
+      if (wb < 0) continue;  // uniform across blocks: every block saw the same candidates
+      const T *x = a.cand_col + ((size_t)buf * G + wb) * a.lds;
+      for (int t = threadIdx.x; t < s; t += blockDim.x) v[t] = x[t];
+      __syncthreads();
+      T ss = T(0);
+      for (int t = j + 1 + threadIdx.x; t < s; t += blockDim.x) ss += v[t] * v[t];
+      ss = block_sum(ss, red_v);
+      if (threadIdx.x == 0) {
+        const T alpha = v[j];
+        T tau = T(0), beta = alpha;
+        if (ss > T(0)) {
+          const T normx = sqrt(alpha * alpha + ss);
+          beta = (alpha >= T(0)) ? -normx : normx;
+          tau = (beta - alpha) / beta;
+        }
+        s_tau = tau;
+        s_beta = beta;
+        if (b == 0) {
+          a.piv[j] = wi;
+          for (int t = 0; t < j; ++t) a.S11[(size_t)t * a.k + j] = v[t];
+          a.S11[(size_t)j * a.k + j] = beta;
+          for (int t = j + 1; t < a.k; ++t) a.S11[(size_t)t * a.k + j] = T(0);
+        }
+        a.sel[wi] = 1;
+      }
+      __syncthreads();
+      const T tau = s_tau, beta = s_beta;
+      if (tau != T(0)) {
+        const T scal = T(1) / (v[j] - beta);
+        for (int t = j + 1 + threadIdx.x; t < s; t += blockDim.x) v[t] *= scal;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) v[j] = T(1);
+      if (b == wb && threadIdx.x == 0) nrm[wi - c0] = T(-1);  // selected
+      __syncthreads();
+      // 4. apply H to own unselected columns, recompute trailing norms
+      if (tau != T(0)) {
+        for (int c = wid; c < ncol; c += nwarp) {
+          if (nrm[c] < T(0)) continue;
+          T *col = slab + (size_t)c * a.s_pad;
+          T w = T(0);
+          for (int t = j + lane; t < s; t += 32) w += v[t] * col[t];
+          w = warp_sum(w) * tau;
+          T acc = T(0);
+          for (int t = j + lane; t < s; t += 32) {
+            const T y = col[t] - w * v[t];
+            col[t] = y;
+            if (t > j) acc += y * y;
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) nrm[c] = acc;
+        }
+      } else {
+        for (int c = wid; c < ncol; c += nwarp) {
+          if (nrm[c] < T(0)) continue;
+          const T *col = slab + (size_t)c * a.s_pad;
+          T acc = T(0);
+          for (int t = j + 1 + lane; t < s; t += 32) acc += col[t] * col[t];
+          acc = warp_sum(acc);
+          if (lane == 0) nrm[c] = acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace ffq

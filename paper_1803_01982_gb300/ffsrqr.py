@@ -1,0 +1,165 @@
+"""Thin Python binding of the C ABI in ``include/ffsrqr.h`` (argument marshalling only).
+
+Every computation happens inside ``libffsrqr.so``; this module passes plain
+pointers, sizes and a CUDA stream.  PyTorch provides device memory and streams.
+If the shared library is missing the import fails loudly: there is no CPU or
+library fallback.
+
+Names mirror the C ABI (``ffsrqr_plan``, ``ffsrqr_run``, ``ffsrqr_destroy``,
+``ffsrqr_status_string``, ``ffsrqr_workspace_item``); ``Plan`` is a small
+convenience wrapper that owns a torch workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PLAIN_FP32 = 0
+MIXED = 1
+FP64 = 3
+
+STATUS = {0: "ok", 1: "rank_deficient", 2: "swap_cap", 3: "timeout", 4: "nonfinite",
+          5: "workspace", 6: "cuda", 7: "unsupported"}
+
+ITEM = {"omega": 0, "bt": 1, "s11": 2, "q1": 3, "gt": 4, "vp": 5, "tmp": 6, "r": 7, "mt": 8}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("max_swaps", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("swaps", ctypes.c_int32),
+                ("g2_first", ctypes.c_double), ("g2_final", ctypes.c_double),
+                ("cand_first", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
+                ("alpha_first", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libffsrqr.so not built ({path}); run __graft_entry__.build() "
+                           "or python -m paper_1803_01982_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    lib.ffsrqr_plan.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, ctypes.POINTER(Opts),
+                                ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_plan.restype = ctypes.c_int
+    lib.ffsrqr_run.argtypes = [P, P, i64, u64, P, i64, P, P, i64, P, P, P, ctypes.POINTER(Info)]
+    lib.ffsrqr_run.restype = ctypes.c_int
+    lib.ffsrqr_destroy.argtypes = [P]
+    lib.ffsrqr_destroy.restype = ctypes.c_int
+    lib.ffsrqr_status_string.argtypes = [ctypes.c_int]
+    lib.ffsrqr_status_string.restype = ctypes.c_char_p
+    lib.ffsrqr_last_cuda_error.argtypes = []
+    lib.ffsrqr_last_cuda_error.restype = ctypes.c_char_p
+    lib.ffsrqr_workspace_item.argtypes = [P, i32, ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    lib.ffsrqr_workspace_item.restype = ctypes.c_int
+    lib.ffsrqr_philox4x32_10.argtypes = [P, P, i32, P]
+    lib.ffsrqr_philox4x32_10.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+# The C names, re-exported unchanged.
+ffsrqr_plan = lib.ffsrqr_plan
+ffsrqr_run = lib.ffsrqr_run
+ffsrqr_destroy = lib.ffsrqr_destroy
+ffsrqr_status_string = lib.ffsrqr_status_string
+ffsrqr_last_cuda_error = lib.ffsrqr_last_cuda_error
+ffsrqr_workspace_item = lib.ffsrqr_workspace_item
+ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
+
+
+class FfsrqrError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = lib.ffsrqr_status_string(rc).decode()
+        if rc == 6:
+            msg += ": " + lib.ffsrqr_last_cuda_error().decode()
+        raise FfsrqrError(f"{what} returned {rc} ({msg})")
+
+
+class Plan:
+    """Plan + device workspace for one (m, n, k, p, mode) shape."""
+
+    def __init__(self, m: int, n: int, k: int, p: int, mode: int = PLAIN_FP32, g: float = 2.0,
+                 max_swaps: int | None = None, flags: int = 0, device=None):
+        import torch
+        self.m, self.n, self.k, self.p, self.mode = m, n, k, p, mode
+        self.device = torch.device("cuda" if device is None else device)
+        self.dtype = torch.float64 if mode == FP64 else torch.float32
+        opts = Opts(g, 4 * k if max_swaps is None else max_swaps, flags)
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        with torch.cuda.device(self.device):
+            _check(lib.ffsrqr_plan(ctypes.byref(self._h), m, n, k, p, mode, ctypes.byref(opts),
+                                   ctypes.byref(ws)), "ffsrqr_plan")
+        self.workspace_bytes = ws.value
+        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
+                                     device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_off = (-base) % 256
+        self._info_host = torch.zeros(ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
+
+    @property
+    def ws_ptr(self) -> int:
+        return self.workspace.data_ptr() + self._ws_off
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.ffsrqr_destroy(h)
+            self._h = None
+
+    def outputs(self):
+        import torch
+        U = torch.empty(self.m, self.k, dtype=self.dtype, device=self.device)
+        S = torch.empty(self.k, dtype=self.dtype, device=self.device)
+        V = torch.empty(self.n, self.k, dtype=self.dtype, device=self.device)
+        piv = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        return U, S, V, piv
+
+    def run(self, A, seed: int = 0, out=None, stream=None):
+        """Enqueue ffsrqr_run on ``stream`` (default: torch's current stream)."""
+        import torch
+        assert A.is_cuda and A.dtype == self.dtype and A.shape == (self.m, self.n)
+        assert A.stride(1) == 1
+        U, S, V, piv = out if out is not None else self.outputs()
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        info_ptr = ctypes.cast(self._info_host.data_ptr(), ctypes.POINTER(Info))
+        _check(lib.ffsrqr_run(self._h, A.data_ptr(), A.stride(0), seed, U.data_ptr(), U.stride(0),
+                              S.data_ptr(), V.data_ptr(), V.stride(0), piv.data_ptr(), self.ws_ptr,
+                              ctypes.c_void_p(st.cuda_stream), info_ptr), "ffsrqr_run")
+        return U, S, V, piv
+
+    def info(self) -> dict:
+        """Report of the last run (call after synchronising its stream)."""
+        return Info.from_buffer_copy(bytes(self._info_host.numpy().tobytes())).as_dict()
+
+    def item(self, name: str):
+        """View of a workspace intermediate (see ffsrqr_workspace_item)."""
+        import torch
+        off = ctypes.c_size_t()
+        r, c, ld = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        eb = ctypes.c_int32()
+        _check(lib.ffsrqr_workspace_item(self._h, ITEM[name], ctypes.byref(off), ctypes.byref(r),
+                                         ctypes.byref(c), ctypes.byref(ld), ctypes.byref(eb)),
+               "ffsrqr_workspace_item")
+        dt = torch.float64 if eb.value == 8 else torch.float32
+        start = self._ws_off + off.value
+        nbytes = (r.value - 1) * ld.value * eb.value + c.value * eb.value
+        raw = self.workspace[start:start + nbytes]
+        flat = raw.view(dt)
+        return torch.as_strided(flat, (r.value, c.value), (ld.value, 1))

@@ -1,0 +1,78 @@
+"""Host-only checks of the C ABI: the library builds, loads, exports every
+function include/*.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(ffsrqr_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def ff():
+    from paper_1803_01982_gb300 import build
+    build.build()
+    from paper_1803_01982_gb300 import ffsrqr
+    return ffsrqr
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["ffsrqr_plan", "ffsrqr_run", "ffsrqr_destroy", "ffsrqr_status_string"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(ff):
+    lib = ctypes.CDLL(ff._build.LIB)
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_status_strings(ff):
+    assert ff.ffsrqr_status_string(0) == b"ok"
+    assert b"swap" in ff.ffsrqr_status_string(2)
+    assert ff.ffsrqr_status_string(-3) == b"invalid argument"
+
+
+@pytest.mark.parametrize("args,code", [
+    ((0, 10, 2, 1, 0), -2),        # m
+    ((10, 0, 2, 1, 0), -3),        # n
+    ((10, 8, 0, 1, 0), -4),        # k = 0
+    ((10, 8, 9, 0, 0), -4),        # k > n
+    ((10, 8, 4, -1, 0), -5),       # p < 0
+    ((10, 8, 4, 7, 0), -5),        # k + p > m
+    ((10, 8, 4, 2, 2), -6),        # mode
+])
+def test_plan_argument_errors(ff, args, code):
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    rc = ff.ffsrqr_plan(ctypes.byref(h), *args, None, ctypes.byref(ws))
+    assert rc == code
+    assert not h.value
+
+
+def test_plan_bad_opts(ff):
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    opts = ff.Opts(1.0, 10, 0)   # g must exceed 1
+    assert ff.ffsrqr_plan(ctypes.byref(h), 10, 8, 3, 2, 0, ctypes.byref(opts), ctypes.byref(ws)) == -7
+    assert ff.ffsrqr_plan(None, 10, 8, 3, 2, 0, None, ctypes.byref(ws)) == -1
+    assert ff.ffsrqr_plan(ctypes.byref(h), 10, 8, 3, 2, 0, None, None) == -8
+
+
+def test_run_and_destroy_null_plan(ff):
+    assert ff.ffsrqr_run(None, None, 0, 0, None, 0, None, None, 0, None, None, None, None) == -1
+    assert ff.ffsrqr_destroy(None) == -1
+    assert ff.ffsrqr_philox4x32_10(None, None, 1, None) == -1
