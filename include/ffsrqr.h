@@ -67,6 +67,10 @@ typedef struct {
   int32_t flags;
 } ffsrqr_opts_t;
 
+/* opts.flags bits */
+#define FFSRQR_FLAG_CHECK_FINITE 1 /* scan A for Inf/NaN first (one extra read of A) */
+#define FFSRQR_FLAG_PHASE_TIMES 2  /* record CUDA events between pipeline phases */
+
 /* Per-run report, written by a device->host copy enqueued at the end of
  * ffsrqr_run; valid after the stream has been synchronised.
  *   g2_first / g2_final: g2 = |alpha| ||Rtilde^{-T}||_{1,2} (Eq. for g1, g2 in
@@ -130,6 +134,16 @@ const char *ffsrqr_last_cuda_error(void);
  * and the element size in bytes.  Returns 0 or -2 for an unknown item. */
 int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,
                           int64_t *cols, int64_t *ld, int32_t *elem_bytes);
+
+/* Per-phase device times (milliseconds) of the last ffsrqr_run of a plan
+ * created with FFSRQR_FLAG_PHASE_TIMES, measured by CUDA events recorded on
+ * the run's stream between phases; call after that stream is synchronised.
+ * Phases: 0 Omega, 1 pass 1 (sketch), 2 QRCP of the sketch, 3 panel QR,
+ * 4 pass 2 (R12), 5 SRQR trailing norms and test, 6 swap loop, 7 QR of
+ * (R11 R12)^T, 8 pass 3 (A Pi Qhat1), 9 QR of tmp, 10 small SVD, 11 U, V and
+ * outputs.  Writes min(cap, 12) values; returns the number written, -1 for a
+ * NULL plan, -2 if the plan was made without the flag. */
+int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap);
 
 /* Raw Philox4x32-10 blocks (Salmon et al., SC'11), the counter-based generator
  * behind Omega (Alg. 2's Gaussian test matrix): for t < count, reads

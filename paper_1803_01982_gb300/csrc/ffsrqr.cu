@@ -35,6 +35,9 @@
 #include "jacobi.cuh"
 #include "philox.cuh"
 #include "qrcp.cuh"
+#include "tc_gemm.cuh"
+
+#include <cudaTypedefs.h>
 
 using namespace ffq;
 
@@ -82,15 +85,24 @@ struct ffsrqr_plan_s {
   size_t off_q1, off_w, off_rc1, off_rc2, off_gt, off_r11, off_rinv, off_zt, off_bjt, off_cbt,
       off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
       off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_part, off_sgnv, off_sgni, off_sgn;
+  size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
   size_t part_cap;  // elements of the split-K buffer
   int qrcp_grid, qrcp_threads;
+  int smem_optin;  // max dynamic shared memory per block (bytes)
   size_t qrcp_smem;
   int qrcp_cols, qrcp_spad;
   int nblk_tn;  // blocks of the trailing-norm kernel
   int nblk_res; // blocks of the SRQR residual kernels
   int nblk_sign;
   Item items[9];
+  cudaEvent_t ev[13];  // phase events (FFSRQR_FLAG_PHASE_TIMES)
+  bool ev_ok;
 };
+
+#define MARK(i)                                                          \
+  do {                                                                   \
+    if (P->ev_ok) cuda_ok(cudaEventRecord(P->ev[(i)], st), "event");     \
+  } while (0)
 
 namespace {
 
@@ -140,6 +152,113 @@ int launch_gemm(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int 
     CKL("splitk_reduce");
   }
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core passes
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D FP32 tensor map over a row-major (outer x inner) array with leading
+// dimension ld (elements), box (box_inner x box_outer), 64B/128B swizzle.
+bool make_map(CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, int64_t ld,
+              int box_inner, int box_outer) {
+  auto fn = encode_fn();
+  if (!fn) {
+    g_last_cuda_error = "cuTensorMapEncodeTiled entry point unavailable";
+    return false;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle swz =
+      (box_inner * 4 == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    g_last_cuda_error = buf;
+    return false;
+  }
+  return true;
+}
+
+
+// D (M x N) = sum_k Aop(m,k) Bop(k,n) on the tensor cores (see tc_gemm.cuh).
+// A: the big matrix (row-major, lda), A_MN selects the contraction over its
+// rows (passes 1, 2) or its columns (pass 3).  Bt / Btl: thin operand (and its
+// TF32 tail for nprod = 3) stored N x K row-major with leading dim ldb.
+int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int nprod, bool a_mn, int M,
+              int N, int K, const float *A, int64_t lda, const float *Bt, const float *Btl, int64_t ldb,
+              float *C, int64_t ldc) {
+  const int BK = (nprod == 1) ? 32 : 16;
+  const int ntile = (int)round_up(N, 16);
+  CUtensorMap mA, mB, mBl;
+  if (a_mn) {
+    // A^T tile: inner = A's column index (M), outer = A's row index (K)
+    if (!make_map(&mA, A, M, K, lda, 32, BK)) return FFSRQR_STATUS_CUDA;
+  } else {
+    if (!make_map(&mA, A, K, M, lda, BK, TC_BM)) return FFSRQR_STATUS_CUDA;
+  }
+  if (!make_map(&mB, Bt, K, N, ldb, BK, ntile)) return FFSRQR_STATUS_CUDA;
+  if (!make_map(&mBl, Btl ? Btl : Bt, K, N, ldb, BK, ntile)) return FFSRQR_STATUS_CUDA;
+  TcSched sc;
+  sc.M = M;
+  sc.N = N;
+  sc.K = K;
+  sc.KB = (int)cdiv(K, BK);
+  sc.tiles = (int)cdiv(M, TC_BM);
+  sc.U = (long long)sc.tiles * sc.KB;
+  sc.G = (int)std::min<long long>(P->num_sms, sc.U);
+  sc.ntile = ntile;
+  sc.ldc = ldc;
+  sc.C = C;
+  sc.part = reinterpret_cast<float *>(ws + P->off_tcpart);
+  sc.ctl = reinterpret_cast<int *>(ws + P->off_ctl);
+  int stage_bytes = 0;
+  if (nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true>::bytes(ntile);
+  else if (nprod == 3 && a_mn) stage_bytes = TcStage<16, 3, true>::bytes(ntile);
+  else stage_bytes = TcStage<16, 3, false>::bytes(ntile);
+  const int budget = P->smem_optin - 2048;  // static shared memory and alignment slack
+  sc.stages = std::min(TC_MAX_STAGES, budget / stage_bytes);
+  if (sc.stages < 2) return FFSRQR_STATUS_UNSUPPORTED;
+  const size_t smem = (size_t)sc.stages * stage_bytes + 1024;
+#define TC_LAUNCH(BKv, NPv, AMNv)                                                                    \
+  {                                                                                                  \
+    auto fn = tc_gemm_kernel<BKv, NPv, AMNv>;                                                        \
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));            \
+    fn<<<sc.G, TC_THREADS, smem, st>>>(mA, mB, mBl, sc);                                             \
+  }
+  if (nprod == 1 && a_mn) TC_LAUNCH(32, 1, true)
+  else if (nprod == 3 && a_mn) TC_LAUNCH(16, 3, true)
+  else if (nprod == 3 && !a_mn) TC_LAUNCH(16, 3, false)
+  else return FFSRQR_STATUS_UNSUPPORTED;
+#undef TC_LAUNCH
+  CKL("tc_gemm");
+  tc_fixup_kernel<<<dim3(sc.tiles, TC_BM / 32), 256, 0, st>>>(sc);
+  CKL("tc_fixup");
+  return 0;
+}
+
+// Whether the tensor-core passes can address A with TMA (16-byte aligned base
+// and row stride); otherwise the CUDA-core passes are used.
+bool tc_ok(const void *A, int64_t lda) {
+  return ((uintptr_t)A % 16 == 0) && (lda % 4 == 0);
 }
 
 template <typename T, bool FWD>
@@ -286,6 +405,31 @@ int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A,
 }
 
 template <typename T>
+bool use_tc(const ffsrqr_plan_s *P, const T *A, int64_t lda) {
+  return sizeof(T) == 4 && P->mode == FFSRQR_MIXED && tc_ok(A, lda);
+}
+
+// Pass 2 (a_mn: G^T = A^T X, X = Q1 with rows = m) or pass 3 (tmp = A X,
+// X = V' with rows = n): X (rows x k, ld ldk) is transposed to K-major and split
+// into its TF32 head and tail, then the 3-product tensor-core pass runs.
+int tc_thin_pass(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, bool a_mn, const float *A,
+                 int64_t lda, const float *X, int64_t rows, float *C) {
+  const int k = P->k;
+  const int64_t ldt = round_up(rows, 4);
+  float *tt = reinterpret_cast<float *>(ws + P->off_tt);
+  float *bh = reinterpret_cast<float *>(ws + P->off_bh);
+  float *bl = reinterpret_cast<float *>(ws + P->off_bl);
+  transpose_kernel<float><<<dim3((unsigned)cdiv(rows, 32), (unsigned)cdiv(k, 32)), dim3(32, 8), 0, st>>>(
+      X, P->ldk, k, rows, tt, ldt);
+  CKL("transpose_thin");
+  split_tf32_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)k * rows, 256), 8 * P->num_sms), 256, 0, st>>>(
+      tt, ldt, k, rows, bh, bl);
+  CKL("split_tf32");
+  const int M = (int)(a_mn ? P->n : P->m);
+  return launch_tc(st, P, ws, 3, a_mn, M, k, (int)rows, A, lda, bh, bl, ldt, C, P->ldk);
+}
+
+template <typename T>
 int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
              int64_t ldv, int32_t *piv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
   const int64_t m = P->m, n = P->n;
@@ -307,16 +451,25 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   }
 
   // a1: Omega
+  MARK(0);
   {
     const int64_t nq = cdiv((int64_t)s * m, 4);
     omega_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(nq, 256), 8 * nsm), 256, 0, st>>>(w.om, s, m, ldm,
                                                                                          seed);
     CKL("omega");
   }
+  const bool tc = use_tc<T>(P, A, lda);
+  MARK(1);
   // a2: pass 1, B^T (n x s) = A^T Omega^T
-  if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, (int)m, A, lda, true, w.om, ldm, false, w.bt, lds)))
+  if (tc) {
+    if ((rc = launch_tc(st, P, ws, 1, true, (int)n, s, (int)m, (const float *)A, lda, (const float *)w.om,
+                        nullptr, ldm, (float *)w.bt, lds)))
+      return rc;
+  } else if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, (int)m, A, lda, true, w.om, ldm, false, w.bt, lds))) {
     return rc;
+  }
   // a3: QRCP on the sketch
+  MARK(2);
   {
     QrcpArgs<T> qa;
     qa.Bt = w.bt;
@@ -342,15 +495,22 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   }
   posdiag_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.s11, k);
   CKL("posdiag");
+  MARK(3);
   // a4: panel Y = A_J S11^{-1}, CholeskyQR2 -> Q1
   gather_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(
       A, lda, m, k, piv, w.q1, ldk);
   CKL("gather_cols");
   if ((rc = launch_trsm<T, true>(st, P, w.q1, ldk, m, w.s11, k, 1))) return rc;
   if ((rc = cholqr2<T>(st, P, ws, w.q1, ldk, m, nullptr))) return rc;
+  MARK(4);
   // a5: pass 2, G^T (n x k) = A^T Q1
-  if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, (int)m, A, lda, true, w.q1, ldk, true, w.gt, ldk)))
+  if (tc) {
+    if ((rc = tc_thin_pass(st, P, ws, true, (const float *)A, lda, (const float *)w.q1, m, (float *)w.gt)))
+      return rc;
+  } else if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, (int)m, A, lda, true, w.q1, ldk, true, w.gt, ldk))) {
     return rc;
+  }
+  MARK(5);
   // a6: R11, R11^{-1}, Z^T = G^T R11^{-T}
   extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11);
   CKL("extract_r11");
@@ -372,14 +532,23 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   if (k < n) {
     if ((rc = srqr_test<T>(st, P, w, A, lda, 1))) return rc;
   }
+  MARK(6);
+  // a7: swap loop (Alg. 4) runs here when g2 > g
+  MARK(7);
   // a8: V' = orth(Z^T), R_z
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.zt, ldk, w.vp,
                                                                                           ldk, n, k);
   CKL("copy_vp");
   if ((rc = cholqr2<T>(st, P, ws, w.vp, ldk, n, w.rz))) return rc;
+  MARK(8);
   // a9: pass 3, tmp (m x k) = A V'
-  if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, (int)n, A, lda, false, w.vp, ldk, true, w.tmp, ldk)))
+  if (tc) {
+    if ((rc = tc_thin_pass(st, P, ws, false, (const float *)A, lda, (const float *)w.vp, n, (float *)w.tmp)))
+      return rc;
+  } else if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, (int)n, A, lda, false, w.vp, ldk, true, w.tmp, ldk))) {
     return rc;
+  }
+  MARK(9);
   // a10: Y_t = tmp R_z^{-T} R11^{-1}; CholeskyQR2 -> Q_t, R_t; M_t = R_t R11 R_z^T
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(w.tmp, ldk, w.yt,
                                                                                           ldk, m, k);
@@ -389,6 +558,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   if ((rc = cholqr2<T>(st, P, ws, w.yt, ldk, m, w.rt))) return rc;
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.rt, k, false, w.r11, k, true, w.t1, k))) return rc;
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.t1, k, false, w.rz, k, false, w.mt, k))) return rc;
+  MARK(10);
   {
     const int kk = k + (k & 1);
     const size_t smem = (size_t)kk * k * sizeof(T) + (size_t)(2 * kk + kk) * sizeof(T) +
@@ -399,6 +569,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
     jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, w.ctl, 40, tol);
     CKL("jacobi_svd");
   }
+  MARK(11);
   // a11: U = Q_t U_s, V = V' V_s, sign rule
   if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, k, w.yt, ldk, false, w.us, k, true, U, ldu))) return rc;
   if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, k, w.vp, ldk, false, w.vs, k, true, V, ldv))) return rc;
@@ -415,6 +586,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   CKL("piv_rest");
   ffsrqr_info_t *dinfo = reinterpret_cast<ffsrqr_info_t *>(ws + P->off_info);
   info_kernel<<<1, 32, 0, st>>>(w.ctl, w.dctl, dinfo);
+  MARK(12);
   CKL("info");
   if (info) CK(cudaMemcpyAsync(info, dinfo, sizeof(ffsrqr_info_t), cudaMemcpyDeviceToHost, st));
   return 0;
@@ -477,6 +649,15 @@ void layout(ffsrqr_plan_s *P) {
   P->off_sgn = take((size_t)k * E);
   P->part_cap = (size_t)std::max<int64_t>((int64_t)k * k * 64, (int64_t)4 * 1024 * 1024 / E);
   P->off_part = take(P->part_cap * E);
+  if (P->mode == FFSRQR_MIXED) {
+    const int64_t ldmax = std::max(round_up(m, 4), round_up(n, 4));
+    P->off_tcpart = take((size_t)2 * nsm * TC_BM * 256 * sizeof(float));
+    P->off_tt = take((size_t)k * ldmax * sizeof(float));
+    P->off_bh = take((size_t)k * ldmax * sizeof(float));
+    P->off_bl = take((size_t)k * ldmax * sizeof(float));
+  } else {
+    P->off_tcpart = P->off_tt = P->off_bh = P->off_bl = 0;
+  }
   P->ws_bytes = off;
   auto item = [&](int i, size_t o, int64_t r, int64_t c, int64_t ld) {
     P->items[i].off = o;
@@ -503,6 +684,7 @@ int plan_qrcp(ffsrqr_plan_s *P) {
   P->qrcp_spad = (int)round_up(s, 4);
   int dev_smem = 0;
   CK(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+  P->smem_optin = dev_smem;
   const size_t budget = (size_t)dev_smem - 2048;
   // slab width per block so that the slab fits; at least 16 columns per block
   int64_t grid = std::min<int64_t>(P->num_sms, std::max<int64_t>(1, cdiv(P->n, 16)));
@@ -570,6 +752,16 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
     delete P;
     return rc;
   }
+  P->ev_ok = false;
+  if (P->flags & FFSRQR_FLAG_PHASE_TIMES) {
+    bool ok = true;
+    for (int i = 0; i < 13 && ok; ++i) ok = cuda_ok(cudaEventCreate(&P->ev[i]), "cudaEventCreate");
+    if (!ok) {
+      delete P;
+      return FFSRQR_STATUS_CUDA;
+    }
+    P->ev_ok = true;
+  }
   if (elem == 8) layout<double>(P);
   else layout<float>(P);
   *workspace_bytes = P->ws_bytes;
@@ -601,6 +793,8 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
 
 int ffsrqr_destroy(ffsrqr_plan_t plan) {
   if (!plan) return -1;
+  if (plan->ev_ok)
+    for (int i = 0; i < 13; ++i) cudaEventDestroy(plan->ev[i]);
   delete plan;
   return 0;
 }
@@ -622,6 +816,18 @@ const char *ffsrqr_status_string(int code) {
 }
 
 const char *ffsrqr_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap) {
+  if (!plan) return -1;
+  if (!plan->ev_ok) return -2;
+  int cnt = 0;
+  for (int i = 0; i < 12 && cnt < cap; ++i, ++cnt) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, plan->ev[i], plan->ev[i + 1]) != cudaSuccess) t = -1.f;
+    ms[cnt] = t;
+  }
+  return cnt;
+}
 
 int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,
                           int64_t *cols, int64_t *ld, int32_t *elem_bytes) {

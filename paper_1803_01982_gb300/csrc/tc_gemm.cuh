@@ -1,0 +1,556 @@
+// tc_gemm.cuh -- the three passes over A on the 5th-generation tensor cores:
+// tcgen05.mma (kind::tf32) with the accumulator in tensor memory (TMEM),
+// operands staged in shared memory by TMA (cp.async.bulk.tensor), a persistent
+// stream-K schedule over (128-row tile, K-block) units, warp-specialised roles.
+//
+//   D (M x N, row-major, FP32) = sum_k Aop(m, k) Bop(k, n)
+//   Aop(m, k): the big matrix A, either stored with m contiguous (A_MN:
+//              element (m,k) at A[k*lda + m]; passes 1 and 2, where the
+//              contraction runs over A's rows) or with k contiguous (element
+//              (m,k) at A[m*lda + k]; pass 3).
+//   Bop(k, n): a thin operand stored K-major as Bt[n*ldb + k] (Omega, Q1^T,
+//              V'^T), N <= 256 columns.
+//   NPROD = 1: one TF32 product (the sketch, pass 1).
+//   NPROD = 3: the split A = Ah + Al, B = Bh + Bl with Ah, Bh exactly
+//              representable in TF32 (low 13 mantissa bits cleared) and
+//              D = Ah Bh + Ah Bl + Al Bh (dropping Al Bl ~ 2^-22 |A||B|), which
+//              restores FP32-level accuracy from TF32 products.  Bh / Bl are
+//              prepared by split_tf32_kernel; Ah / Al are formed in shared
+//              memory by the converter warps.
+//
+// The MMA always reads both operands K-major (the tf32 MMA is used without its
+// transpose mode).  For A_MN the TMA lands the tile m-contiguous (four boxes of
+// 32 m x BK k, 128-byte swizzle) and the converter warps transpose it in shared
+// memory into the K-major swizzled layout the MMA reads (splitting it into
+// Ah / Al on the way when NPROD = 3); for pass 3 the TMA lands A K-major and
+// the converters only split it in place.
+//
+// Warp roles (12 warps): 0 = TMA producer, 1 = MMA issuer (one thread), 2 =
+// TMEM allocation owner, 3 = idle, 4..7 = epilogue (TMEM -> registers ->
+// global; warp w reads TMEM lanes 32*(w%4)..+31), 8..11 = converters.
+//
+// Stream-K: unit u = tile*KB + kb; block c owns units [U*c/G, U*(c+1)/G).  A
+// block's first and last segments may cover part of a tile's K range; those
+// partial tiles go to part[(2c + slot)] and tc_fixup_kernel adds the pieces of
+// each tile in block order (deterministic).  All other tiles are written
+// directly.  Every mbarrier wait is bounded (~1 s); on expiry the block
+// records STATUS_TIMEOUT, drains what it issued, frees its TMEM and exits.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ffq {
+
+constexpr int TC_BM = 128;
+constexpr int TC_THREADS = 384;
+constexpr int TC_MAX_STAGES = 6;
+constexpr long long TC_SPIN = 4000000;
+
+struct TcSched {
+  int M, N, K;      // problem
+  int KB;           // K blocks
+  int tiles;        // ceil(M / 128)
+  long long U;      // tiles * KB
+  int G;            // grid
+  int ntile;        // N rounded up to a multiple of 16 (MMA N)
+  int stages;       // pipeline depth (<= TC_MAX_STAGES)
+  int64_t ldc;
+  float *C;
+  float *part;      // [2G][128][ntile]
+  int *ctl;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (~1 s of wall time, whatever try_wait's internal suspend time
+// is); returns false and flags the timeout if it expires, or returns false at
+// once if another role already flagged one.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *ctl) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  long long spins = 0;
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if ((++spins & 255) == 0 && (globaltimer_ns() - t0 > 1000000000ull || spins > TC_SPIN)) {
+      *abort_flag = 1;
+      atomicExch(ctl + CTL_TIMEOUT, 1);
+      set_status(ctl, STATUS_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Wait (at most ~1 s) without touching the abort state: used while draining.
+__device__ __forceinline__ void mbar_wait_quiet(uint64_t *bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer_ns();
+  long long spins = 0;
+  while (!mbar_try(bar, parity)) {
+    if ((++spins & 255) == 0 && (globaltimer_ns() - t0 > 1000000000ull || spins > TC_SPIN)) return;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(smem_dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, leading / stride
+// byte offsets (>> 4), version 1, swizzle mode (2 = 128B, 4 = 64B).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swz << 61);
+}
+
+// Instruction descriptor, kind::tf32, FP32 accumulate, M = 128, both operands
+// K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Segment iterator shared by all roles: block c walks units [u0, u1).
+struct SegIter {
+  long long u, u1;
+  int KB;
+  __device__ bool next(int &tile, int &kb0, int &kb1) {
+    if (u >= u1) return false;
+    tile = (int)(u / KB);
+    kb0 = (int)(u - (long long)tile * KB);
+    const long long left = u1 - u;
+    kb1 = (int)((long long)kb0 + left < KB ? kb0 + left : KB);
+    u += kb1 - kb0;
+    return true;
+  }
+};
+
+// Byte offset of element (row r, column k) in a K-major tile whose rows are
+// BK FP32 values (128 B for BK = 32 with the 128B swizzle, 64 B for BK = 16
+// with the 64B swizzle): the 16-byte chunk index is XORed with address bits
+// 7..9 (128B) or 7..8 (64B), as TMA writes and the MMA reads it.
+template <int BK>
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k) {
+  if (BK == 32) return (uint32_t)(r * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + ((k & 3) << 2));
+  return (uint32_t)(r * 64 + ((((k >> 2) ^ ((r >> 1) & 3)) & 3) << 4) + ((k & 3) << 2));
+}
+// Byte offset of element (k, m) in the m-contiguous TMA landing tile: four
+// boxes of 32 m x BK k rows of 128 B, 128B swizzle.
+template <int BK>
+__device__ __forceinline__ uint32_t mn_off(int k, int m) {
+  const int q = m >> 5, ml = m & 31;
+  return (uint32_t)(q * (BK * 128) + k * 128 + ((((ml >> 2) ^ (k & 7)) & 7) << 4) + ((ml & 3) << 2));
+}
+
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Shared memory of one stage: [raw A landing (A_MN only)] [Ah] [Al (NPROD 3)]
+// [Bh] [Bl (NPROD 3)]; every piece is a multiple of 1024 bytes.
+template <int BK, int NPROD, bool A_MN>
+struct TcStage {
+  static constexpr int A_BYTES = TC_BM * BK * 4;
+  static constexpr int RAW = A_MN ? A_BYTES : 0;
+  static constexpr int AH = RAW;
+  static constexpr int AL = AH + A_BYTES;
+  static constexpr int BH = AH + A_BYTES * (NPROD == 3 ? 2 : 1);
+  __host__ __device__ static constexpr int b_bytes(int nt) { return nt * BK * 4; }
+  __host__ __device__ static constexpr int bytes(int nt) { return BH + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
+  __host__ __device__ static constexpr int tx(int nt) { return A_BYTES + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
+  static constexpr bool CONVERT = A_MN || NPROD == 3;
+};
+
+template <int BK, int NPROD, bool A_MN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmBl, TcSched sc) {
+  using S = TcStage<BK, NPROD, A_MN>;
+  constexpr int A_BYTES = S::A_BYTES;
+  constexpr int KSWZ = (BK == 32) ? 2 : 4;  // 128B / 64B swizzle of K-major rows
+  constexpr int KROW = BK * 4;
+  const int NT = sc.ntile;
+  const int STAGES = sc.stages;
+  const int B_BYTES = S::b_bytes(NT);
+  const int STAGE_BYTES = S::bytes(NT);
+  const uint32_t TX_BYTES = (uint32_t)S::tx(NT);
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[TC_MAX_STAGES], conv_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], drain_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x;
+  SegIter it;
+  it.u = (sc.U * c) / sc.G;
+  it.u1 = (sc.U * (c + 1)) / sc.G;
+  it.KB = sc.KB;
+  const int first_tile = (int)(it.u / sc.KB);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&conv_bar[s], 4);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 4);
+    }
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  volatile int *abortp = &abort_flag;
+
+  auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE_BYTES; };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int tile, kb0, kb1;
+      SegIter my = it;
+      bool ok = true;
+      uint32_t issued = 0, issued_ph = 0;  // per stage: a load in flight, and its phase parity
+      while (ok && my.next(tile, kb0, kb1)) {
+        for (int kb = kb0; kb < kb1 && ok; ++kb) {
+          if (!mbar_wait(&empty_bar[s], ph ^ 1u, abortp, sc.ctl)) {
+            ok = false;
+            break;
+          }
+          issued |= 1u << s;
+          issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+          unsigned char *st = stage_ptr(s);
+          mbar_expect_tx(&full_bar[s], TX_BYTES);
+          const int k0 = kb * BK, m0 = tile * TC_BM;
+          if (A_MN) {
+#pragma unroll
+            for (int q = 0; q < TC_BM / 32; ++q)
+              tma_load_2d(st + q * (BK * 128), &tmA, m0 + 32 * q, k0, &full_bar[s]);
+          } else {
+            tma_load_2d(st + S::AH, &tmA, k0, m0, &full_bar[s]);
+          }
+          tma_load_2d(st + S::BH, &tmB, k0, 0, &full_bar[s]);
+          if (NPROD == 3) tma_load_2d(st + S::BH + B_BYTES, &tmBl, k0, 0, &full_bar[s]);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        for (int d = 0; d < STAGES; ++d)
+          if (issued & (1u << d)) mbar_wait_quiet(&full_bar[d], (issued_ph >> d) & 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int seg = 0;
+      int tile, kb0, kb1;
+      SegIter my = it;
+      const uint32_t IDESC = idesc_tf32(NT);
+      bool ok = true;
+      while (ok && my.next(tile, kb0, kb1)) {
+        const int b = seg & 1;
+        const uint32_t acc_ph = (uint32_t)((seg >> 1) & 1);
+        if (!mbar_wait(&acce_bar[b], acc_ph ^ 1u, abortp, sc.ctl)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(b * 256);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          uint64_t *wb = S::CONVERT ? &conv_bar[s] : &full_bar[s];
+          if (!mbar_wait(wb, ph, abortp, sc.ctl)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(stage_ptr(s));
+          const uint32_t ah = base + S::AH, al = base + S::AL, bh = base + S::BH, bl = bh + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 8; ++kk) {
+            // K-major operands: rows of BK*4 bytes in 8-row groups; K step of
+            // one MMA (8 TF32 values) = 32 bytes within the swizzled row.
+            const uint64_t da = smem_desc(ah + kk * 32, 16, 8 * KROW, KSWZ);
+            const uint64_t db = smem_desc(bh + kk * 32, 16, 8 * KROW, KSWZ);
+            const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
+            mma_tf32(dt, da, db, IDESC, acc);
+            if (NPROD == 3) {
+              const uint64_t dal = smem_desc(al + kk * 32, 16, 8 * KROW, KSWZ);
+              const uint64_t dbl = smem_desc(bl + kk * 32, 16, 8 * KROW, KSWZ);
+              mma_tf32(dt, da, dbl, IDESC, 1u);
+              mma_tf32(dt, dal, db, IDESC, 1u);
+            }
+          }
+          mma_commit(&empty_bar[s]);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&accf_bar[b]);
+        ++seg;
+      }
+      if (*abortp) {
+        // make sure no MMA is still writing TMEM before it is freed
+        mma_commit(&drain_bar);
+        mbar_wait_quiet(&drain_bar, 0);
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;
+    int seg = 0;
+    int tile, kb0, kb1;
+    SegIter my = it;
+    while (my.next(tile, kb0, kb1)) {
+      const int b = seg & 1;
+      const uint32_t acc_ph = (uint32_t)((seg >> 1) & 1);
+      if (!mbar_wait(&accf_bar[b], acc_ph, abortp, sc.ctl)) break;
+      tc_fence_after();
+      const int row_in_tile = q * 32 + lane;
+      const int row = tile * TC_BM + row_in_tile;
+      const bool full = (kb0 == 0 && kb1 == sc.KB);
+      float *dst;
+      int ncols;
+      if (full) {
+        dst = (row < sc.M) ? sc.C + (int64_t)row * sc.ldc : nullptr;
+        ncols = sc.N;
+      } else {
+        const int slot = (tile == first_tile) ? 0 : 1;
+        dst = sc.part + ((int64_t)(2 * c + slot) * TC_BM + row_in_tile) * sc.ntile;
+        ncols = sc.ntile;
+      }
+#pragma unroll 1
+      for (int c0 = 0; c0 < NT; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + c0), v);
+        if (dst) {
+          if (c0 + 32 <= ncols) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst + c0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < ncols) dst[c0 + i] = v[i];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[b]);
+      ++seg;
+    }
+  } else if (warp >= 8 && S::CONVERT) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 256;  // 0..127: tile row m (A_MN) or 16-byte chunk index
+    int s = 0;
+    uint32_t ph = 0;
+    int tile, kb0, kb1;
+    SegIter my = it;
+    bool ok = true;
+    while (ok && my.next(tile, kb0, kb1)) {
+      for (int kb = kb0; kb < kb1; ++kb) {
+        if (!mbar_wait(&full_bar[s], ph, abortp, sc.ctl)) {
+          ok = false;
+          break;
+        }
+        unsigned char *st = stage_ptr(s);
+        if (A_MN) {
+          // transpose row m = ct of the m-contiguous tile into K-major rows
+          const int m = ct;
+#pragma unroll
+          for (int k4 = 0; k4 < BK; k4 += 4) {
+            float x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = *reinterpret_cast<const float *>(st + mn_off<BK>(k4 + j, m));
+            const uint32_t o = kmajor_off<BK>(m, k4);
+            if (NPROD == 3) {
+              float4 h, l;
+              h.x = tf32_head(x[0]);
+              h.y = tf32_head(x[1]);
+              h.z = tf32_head(x[2]);
+              h.w = tf32_head(x[3]);
+              l.x = x[0] - h.x;
+              l.y = x[1] - h.y;
+              l.z = x[2] - h.z;
+              l.w = x[3] - h.w;
+              *reinterpret_cast<float4 *>(st + S::AH + o) = h;
+              *reinterpret_cast<float4 *>(st + S::AL + o) = l;
+            } else {
+              *reinterpret_cast<float4 *>(st + S::AH + o) = make_float4(x[0], x[1], x[2], x[3]);
+            }
+          }
+        } else {
+          // split the K-major tile in place: Ah (TF32 head) and Al (tail)
+          float4 *a4 = reinterpret_cast<float4 *>(st + S::AH);
+          float4 *l4 = reinterpret_cast<float4 *>(st + S::AL);
+#pragma unroll 4
+          for (int i = ct; i < A_BYTES / 16; i += 128) {
+            const float4 x = a4[i];
+            float4 h, l;
+            h.x = tf32_head(x.x);
+            h.y = tf32_head(x.y);
+            h.z = tf32_head(x.z);
+            h.w = tf32_head(x.w);
+            l.x = x.x - h.x;
+            l.y = x.y - h.y;
+            l.z = x.z - h.z;
+            l.w = x.w - h.w;
+            a4[i] = h;
+            l4[i] = l;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv_bar[s]);
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+  }
+  // teardown
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// Sum the partial pieces of the tiles that several blocks share, in block
+// order, and write them to C.  One block per (tile, 32-row slab).
+__global__ void tc_fixup_kernel(TcSched sc) {
+  const int tile = blockIdx.x;
+  const long long ua = (long long)tile * sc.KB, ub = ua + sc.KB - 1;
+  auto owner = [&](long long u) {
+    long long lo = 0, hi = sc.G - 1;
+    while (lo < hi) {
+      const long long mid = (lo + hi + 1) / 2;
+      if ((sc.U * mid) / sc.G <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    return (int)lo;
+  };
+  const int c_lo = owner(ua), c_hi = owner(ub);
+  if (c_lo == c_hi) return;  // written directly by its only owner
+  const int r0 = blockIdx.y * 32;
+  for (int e = threadIdx.x; e < 32 * sc.N; e += blockDim.x) {
+    const int rr = r0 + e / sc.N, col = e % sc.N;
+    const int row = tile * TC_BM + rr;
+    if (row >= sc.M) continue;
+    float acc = 0.f;
+    for (int cb = c_lo; cb <= c_hi; ++cb) {
+      const int ft = (int)(((sc.U * cb) / sc.G) / sc.KB);
+      const int slot = (tile == ft) ? 0 : 1;
+      acc += sc.part[((int64_t)(2 * cb + slot) * TC_BM + rr) * sc.ntile + col];
+    }
+    sc.C[(int64_t)row * sc.ldc + col] = acc;
+  }
+}
+
+// Bh = TF32-exact head of B (low 13 mantissa bits cleared), Bl = B - Bh
+// (exact in FP32), over a rows x cols block with leading dimension ld.
+__global__ void split_tf32_kernel(const float *__restrict__ B, int64_t ld, int64_t rows, int64_t cols,
+                                  float *__restrict__ Bh, float *__restrict__ Bl) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    const float x = B[i * ld + j];
+    const float h = tf32_head(x);
+    Bh[i * ld + j] = h;
+    Bl[i * ld + j] = x - h;
+  }
+}
+
+}  // namespace ffq

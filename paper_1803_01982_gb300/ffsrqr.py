@@ -64,6 +64,8 @@ def _load():
     lib.ffsrqr_workspace_item.restype = ctypes.c_int
     lib.ffsrqr_philox4x32_10.argtypes = [P, P, i32, P]
     lib.ffsrqr_philox4x32_10.restype = ctypes.c_int
+    lib.ffsrqr_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
+    lib.ffsrqr_phase_times.restype = ctypes.c_int
     return lib
 
 
@@ -77,6 +79,7 @@ ffsrqr_status_string = lib.ffsrqr_status_string
 ffsrqr_last_cuda_error = lib.ffsrqr_last_cuda_error
 ffsrqr_workspace_item = lib.ffsrqr_workspace_item
 ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
+ffsrqr_phase_times = lib.ffsrqr_phase_times
 
 
 class FfsrqrError(RuntimeError):
@@ -163,3 +166,18 @@ class Plan:
         raw = self.workspace[start:start + nbytes]
         flat = raw.view(dt)
         return torch.as_strided(flat, (r.value, c.value), (ld.value, 1))
+
+
+PHASES = ["omega", "pass1_sketch", "qrcp", "panel_qr", "pass2_r12", "srqr_test", "swap_loop",
+          "qr_rt", "pass3_tmp", "qr_tmp", "small_svd", "outputs"]
+FLAG_CHECK_FINITE = 1
+FLAG_PHASE_TIMES = 2
+
+
+def phase_times(plan: "Plan") -> dict:
+    """Per-phase device milliseconds of the plan's last run (FLAG_PHASE_TIMES)."""
+    buf = (ctypes.c_float * 12)()
+    cnt = lib.ffsrqr_phase_times(plan._h, buf, 12)
+    if cnt < 0:
+        raise FfsrqrError("plan was created without FLAG_PHASE_TIMES")
+    return {PHASES[i]: buf[i] for i in range(cnt)}
