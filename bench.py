@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Flip-Flop SRQR library: rank-k approximations per second.
+
+Workload (default): A = U_r diag(sigma) V_r^T + E, m = n = 20000, r = 2000,
+sigma_j = j^-1.5 (slow decay), E ~ N(0, 1e-6^2), FP32, target rank k = 200,
+oversampling p = 10, FFSRQR_MIXED arithmetic.  A (1.6 GB) is larger than the
+129 MB L2, so no flush is needed between steps.  One step = one call of
+ffsrqr_run (all pipeline steps: sketch, QRCP, panel QR, R12 pass, SRQR test,
+QR of (R11 R12)^T, A Pi Qhat1 pass, small SVD, U and V).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+paper's algorithm) on the host cores, on a bounded sample of the same workload,
+and reports its throughput scaled to the full workload.  With more than one GPU
+the replicas run independently (the method has no data-path exchange).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rank-k approx/s"
+UNIT = "approx/s"
+SAMPLE_M, SAMPLE_N = 6000, 1200   # bounded CPU sample (rows x columns of the same recipe)
+
+
+def flops_model(m, n, k, s):
+    """Operation count used to scale CPU samples: the three products over A
+    (2mn(s + 2k), Sec. 3.2's 4mnl + 2(b+p)mn with l = b = k) plus the
+    Householder factorisations with explicit Q of the m x k panel, the m x k tmp
+    and the n x k (R11 R12)^T (8mk^2 + 4nk^2)."""
+    return 2.0 * m * n * (s + 2 * k) + 8.0 * m * k * k + 4.0 * n * k * k
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
+    ap.add_argument("--decay", choices=["slow", "fast"], default="slow")
+    ap.add_argument("--m", type=int, default=20000)
+    ap.add_argument("--n", type=int, default=20000)
+    ap.add_argument("--k", type=int, default=200)
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    d = "sigma_j=j^-1.5" if a.decay == "slow" else "sigma_j=0.97^j"
+    return f"FFSRQR rank-{a.k} of {a.m}x{a.n} FP32, r=2000, {d}, E~N(0,1e-6^2)"
+
+
+def spectrum(a, r):
+    from paper_1803_01982_gb300 import synth
+    return synth.slow_decay(r) if a.decay == "slow" else synth.fast_decay(r)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample
+# --------------------------------------------------------------------------
+def oracle_sample(a, reps=1):
+    import numpy as np
+
+    import oracle
+    from paper_1803_01982_gb300 import synth
+    oracle.build()
+    r = min(2000, SAMPLE_M, SAMPLE_N)
+    A = synth.decayed(SAMPLE_M, SAMPLE_N, spectrum(a, r), 1e-6, seed=1, dtype=np.float32)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.ffsrqr(A, a.k, a.p, seed=0)
+        times.append(time.perf_counter() - t0)
+    s = a.k + a.p
+    scale = flops_model(SAMPLE_M, SAMPLE_N, a.k, s) / flops_model(a.m, a.n, a.k, s)
+    return times, scale
+
+
+def cores_used():
+    env = os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env else (os.cpu_count() or 1)
+
+
+def sample_text(a):
+    return (f"FP64 oracle on a {SAMPLE_M}x{SAMPLE_N} matrix of the same recipe (k={a.k}, p={a.p}); "
+            f"time scaled to {a.m}x{a.n} by the operation-count model "
+            "2mn(s+2k) + 8mk^2 + 4nk^2")
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+def clocks_start(dev_index):
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    os.close(fd)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--id={dev_index}", f"--query-gpu={q}",
+                              "--format=csv,noheader,nounits", "-lms", "50"],
+                             stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, path
+
+
+def clocks_stop(p, path):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# roofline inputs
+# --------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the tensor-core kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "tc_pass_traffic.json")
+    src = os.path.join(ROOT, "paper_1803_01982_gb300", "csrc", "tc_gemm.cuh")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("source_sha256") != sha:
+            return None
+        return d.get("traffic_bytes_per_launch", {}).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    times, scale = oracle_sample(a, reps=a.warmup + a.steps)
+    timed = times[a.warmup:]
+    per_full = statistics.mean(timed) / scale
+    val = 1.0 / per_full
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(a),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                             "sample": sample_text(a)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(a):
+    return {"workload": workload_name(a), "m": a.m, "n": a.n, "k": a.k, "p": a.p,
+            "mode": a.mode, "l2": "inputs larger than L2 (A is 1.6 GB), no flush",
+            "parallelism": f"replicas x{a.gpus}"}
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_01982_gb300 import ffsrqr, synth
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    r = min(2000, a.m, a.n)
+    A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=1 + rank, device=str(dev))
+    plan = ffsrqr.Plan(a.m, a.n, a.k, a.p, mode, flags=ffsrqr.FLAG_PHASE_TIMES, device=dev)
+    out = plan.outputs()
+    st = torch.cuda.current_stream(dev)
+    for _ in range(a.warmup):
+        plan.run(A, 0, out)
+    torch.cuda.synchronize(dev)
+    launches_per_step = ffsrqr.ffsrqr_launch_count(plan._h)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk, clk_path = clocks_start(dev.index if dev.index is not None else 0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phase_sum = None
+    ev0.record(st)
+    for _ in range(a.steps):
+        plan.run(A, 0, out)
+        # per-step phase events are read back (kernel timing for the roofline);
+        # the host wait between steps is small next to a step
+        torch.cuda.synchronize(dev)
+        ph = ffsrqr.phase_times(plan)
+        phase_sum = ph if phase_sum is None else {k: phase_sum[k] + v for k, v in ph.items()}
+    ev1.record(st)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = clocks_stop(clk, clk_path)
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = plan.info()
+    value = world * 1000.0 / ms
+    phases = {k: v / a.steps for k, v in phase_sum.items()}
+
+    # roofline: the dominant pass kernel (one read of A per launch)
+    bytes_per_launch = float(a.m) * a.n * 4
+    if mode == ffsrqr.MIXED:
+        keys = ["tc_pass1_kernel", "tc_pass2_kernel", "tc_pass3_kernel"]
+    else:
+        keys = ["pass1_sketch", "pass2_r12", "pass3_tmp"]
+    dom = max(keys, key=lambda k: phases[k])
+    peak, peak_src = peaks()
+    achieved = bytes_per_launch / (phases[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "traffic": ncu_traffic(dom) if mode == ffsrqr.MIXED else None,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+    three_pass_ms = 3 * bytes_per_launch / (peak * 1e9) * 1e3
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if a.e2e_steps > 0:
+        Ah = A.cpu().pin_memory()
+        host_out = [t.cpu().pin_memory() for t in out]
+        for _ in range(1):
+            A.copy_(Ah, non_blocking=True)
+            plan.run(A, 0, out)
+            for h, d in zip(host_out, out):
+                h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(a.e2e_steps):
+            A.copy_(Ah, non_blocking=True)
+            plan.run(A, 0, out)
+            for h, d in zip(host_out, out):
+                h.copy_(d, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ems = e0.elapsed_time(e1) / a.e2e_steps
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        d2h = sum(t.numel() * t.element_size() for t in out)
+        e2e = {"value": world * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 4,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        times, scale = oracle_sample(a, reps=1)
+        cpu = {"value": scale / times[0], "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+               "sample": sample_text(a), "sample_seconds": times[0]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(a),
+                "roofline": roof,
+                "three_pass_roofline": {"ms": three_pass_ms, "frac_of_step": three_pass_ms / ms},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * a.steps,
+                "clocks": clocks, "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+                "status": info["status"], "swaps": info["swaps"], "g2": info["g2_first"]}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,9 +141,13 @@ int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int6
  * Phases: 0 Omega, 1 pass 1 (sketch), 2 QRCP of the sketch, 3 panel QR,
  * 4 pass 2 (R12), 5 SRQR trailing norms and test, 6 swap loop, 7 QR of
  * (R11 R12)^T, 8 pass 3 (A Pi Qhat1), 9 QR of tmp, 10 small SVD, 11 U, V and
- * outputs.  Writes min(cap, 12) values; returns the number written, -1 for a
- * NULL plan, -2 if the plan was made without the flag. */
+ * outputs; then 12..14 the tensor-core kernels of passes 1, 2, 3 alone (-1
+ * outside FFSRQR_MIXED).  Writes min(cap, 15) values; returns the number
+ * written, -1 for a NULL plan, -2 if the plan was made without the flag. */
 int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap);
+
+/* Number of kernels the last ffsrqr_run of this plan enqueued (-1 for NULL). */
+int ffsrqr_launch_count(ffsrqr_plan_t plan);
 
 /* Raw Philox4x32-10 blocks (Salmon et al., SC'11), the counter-based generator
  * behind Omega (Alg. 2's Gaussian test matrix): for t < count, reads

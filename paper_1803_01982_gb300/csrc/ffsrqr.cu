@@ -58,8 +58,12 @@ bool cuda_ok(cudaError_t e, const char *what) {
     if (!cuda_ok((call), #call)) return FFSRQR_STATUS_CUDA; \
   } while (0)
 
+// Kernel launches enqueued by the current ffsrqr_run on this thread.
+thread_local int g_launches = 0;
+
 #define CKL(what)                                             \
   do {                                                        \
+    ++g_launches;                                             \
     if (!cuda_ok(cudaGetLastError(), what)) return FFSRQR_STATUS_CUDA; \
   } while (0)
 
@@ -96,6 +100,8 @@ struct ffsrqr_plan_s {
   int nblk_sign;
   Item items[9];
   cudaEvent_t ev[13];  // phase events (FFSRQR_FLAG_PHASE_TIMES)
+  cudaEvent_t ev_tc[3][2];  // around each tensor-core pass kernel
+  int launches;        // kernel launches of the last run
   bool ev_ok;
 };
 
@@ -203,7 +209,7 @@ bool make_map(CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, 
 // A: the big matrix (row-major, lda), A_MN selects the contraction over its
 // rows (passes 1, 2) or its columns (pass 3).  Bt / Btl: thin operand (and its
 // TF32 tail for nprod = 3) stored N x K row-major with leading dim ldb.
-int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int nprod, bool a_mn, int M,
+int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pass, int nprod, bool a_mn, int M,
               int N, int K, const float *A, int64_t lda, const float *Bt, const float *Btl, int64_t ldb,
               float *C, int64_t ldc) {
   const int BK = (nprod == 1) ? 32 : 16;
@@ -242,7 +248,9 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int np
   {                                                                                                  \
     auto fn = tc_gemm_kernel<BKv, NPv, AMNv>;                                                        \
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));            \
+    if (P->ev_ok) cudaEventRecord(P->ev_tc[pass][0], st);                                            \
     fn<<<sc.G, TC_THREADS, smem, st>>>(mA, mB, mBl, sc);                                             \
+    if (P->ev_ok) cudaEventRecord(P->ev_tc[pass][1], st);                                            \
   }
   if (nprod == 1 && a_mn) TC_LAUNCH(32, 1, true)
   else if (nprod == 3 && a_mn) TC_LAUNCH(16, 3, true)
@@ -426,7 +434,7 @@ int tc_thin_pass(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, boo
       tt, ldt, k, rows, bh, bl);
   CKL("split_tf32");
   const int M = (int)(a_mn ? P->n : P->m);
-  return launch_tc(st, P, ws, 3, a_mn, M, k, (int)rows, A, lda, bh, bl, ldt, C, P->ldk);
+  return launch_tc(st, P, ws, a_mn ? 1 : 2, 3, a_mn, M, k, (int)rows, A, lda, bh, bl, ldt, C, P->ldk);
 }
 
 template <typename T>
@@ -462,7 +470,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   MARK(1);
   // a2: pass 1, B^T (n x s) = A^T Omega^T
   if (tc) {
-    if ((rc = launch_tc(st, P, ws, 1, true, (int)n, s, (int)m, (const float *)A, lda, (const float *)w.om,
+    if ((rc = launch_tc(st, P, ws, 0, 1, true, (int)n, s, (int)m, (const float *)A, lda, (const float *)w.om,
                         nullptr, ldm, (float *)w.bt, lds)))
       return rc;
   } else if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, (int)m, A, lda, true, w.om, ldm, false, w.bt, lds))) {
@@ -756,6 +764,7 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
   if (P->flags & FFSRQR_FLAG_PHASE_TIMES) {
     bool ok = true;
     for (int i = 0; i < 13 && ok; ++i) ok = cuda_ok(cudaEventCreate(&P->ev[i]), "cudaEventCreate");
+    for (int i = 0; i < 6 && ok; ++i) ok = cuda_ok(cudaEventCreate(&P->ev_tc[i / 2][i % 2]), "cudaEventCreate");
     if (!ok) {
       delete P;
       return FFSRQR_STATUS_CUDA;
@@ -784,17 +793,23 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   if (!workspace || ((uintptr_t)workspace & 255u)) return -11;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
+  g_launches = 0;
+  int rc;
   if (plan->elem == 8)
-    return run_impl<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S,
-                            (double *)V, ldv, piv, ws, st, info);
-  return run_impl<float>(plan, (const float *)A, lda, seed, (float *)U, ldu, (float *)S, (float *)V,
-                         ldv, piv, ws, st, info);
+    rc = run_impl<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S, (double *)V,
+                          ldv, piv, ws, st, info);
+  else
+    rc = run_impl<float>(plan, (const float *)A, lda, seed, (float *)U, ldu, (float *)S, (float *)V, ldv,
+                         piv, ws, st, info);
+  plan->launches = g_launches;
+  return rc;
 }
 
 int ffsrqr_destroy(ffsrqr_plan_t plan) {
   if (!plan) return -1;
   if (plan->ev_ok)
     for (int i = 0; i < 13; ++i) cudaEventDestroy(plan->ev[i]);
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(plan->ev_tc[i / 2][i % 2]);
   delete plan;
   return 0;
 }
@@ -826,7 +841,19 @@ int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap) {
     if (cudaEventElapsedTime(&t, plan->ev[i], plan->ev[i + 1]) != cudaSuccess) t = -1.f;
     ms[cnt] = t;
   }
+  for (int i = 0; i < 3 && cnt < cap; ++i, ++cnt) {
+    float t = -1.f;
+    if (plan->mode == FFSRQR_MIXED &&
+        cudaEventElapsedTime(&t, plan->ev_tc[i][0], plan->ev_tc[i][1]) != cudaSuccess)
+      t = -1.f;
+    ms[cnt] = t;
+  }
   return cnt;
+}
+
+int ffsrqr_launch_count(ffsrqr_plan_t plan) {
+  if (!plan) return -1;
+  return plan->launches;
 }
 
 int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,

@@ -66,6 +66,8 @@ def _load():
     lib.ffsrqr_philox4x32_10.restype = ctypes.c_int
     lib.ffsrqr_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
     lib.ffsrqr_phase_times.restype = ctypes.c_int
+    lib.ffsrqr_launch_count.argtypes = [P]
+    lib.ffsrqr_launch_count.restype = ctypes.c_int
     return lib
 
 
@@ -80,6 +82,7 @@ ffsrqr_last_cuda_error = lib.ffsrqr_last_cuda_error
 ffsrqr_workspace_item = lib.ffsrqr_workspace_item
 ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
 ffsrqr_phase_times = lib.ffsrqr_phase_times
+ffsrqr_launch_count = lib.ffsrqr_launch_count
 
 
 class FfsrqrError(RuntimeError):
@@ -169,15 +172,16 @@ class Plan:
 
 
 PHASES = ["omega", "pass1_sketch", "qrcp", "panel_qr", "pass2_r12", "srqr_test", "swap_loop",
-          "qr_rt", "pass3_tmp", "qr_tmp", "small_svd", "outputs"]
+          "qr_rt", "pass3_tmp", "qr_tmp", "small_svd", "outputs",
+          "tc_pass1_kernel", "tc_pass2_kernel", "tc_pass3_kernel"]
 FLAG_CHECK_FINITE = 1
 FLAG_PHASE_TIMES = 2
 
 
 def phase_times(plan: "Plan") -> dict:
     """Per-phase device milliseconds of the plan's last run (FLAG_PHASE_TIMES)."""
-    buf = (ctypes.c_float * 12)()
-    cnt = lib.ffsrqr_phase_times(plan._h, buf, 12)
+    buf = (ctypes.c_float * 15)()
+    cnt = lib.ffsrqr_phase_times(plan._h, buf, 15)
     if cnt < 0:
         raise FfsrqrError("plan was created without FLAG_PHASE_TIMES")
     return {PHASES[i]: buf[i] for i in range(cnt)}

@@ -41,22 +41,20 @@ def decayed(m: int, n: int, sigma, noise: float = 0.0, seed: int = 1,
 
 
 def decayed_torch(m: int, n: int, sigma, noise: float, seed: int, device: str = "cuda"):
-    """Same recipe as ``decayed`` for sizes too large for the host (20000^2):
-    built on the device with torch's seeded generator (input synthesis only,
-    not the factorisation path), FP64 then rounded once to FP32."""
+    """Same recipe as ``decayed`` for sizes too large to assemble on the host
+    (20000^2): the orthonormal factors come from numpy (seeded Gaussians, QR on
+    the host), the product and the noise are formed on the device in FP64 with
+    torch's seeded generator, then rounded once to FP32.  Input synthesis only,
+    not the factorisation path."""
     import torch
-    sigma = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device)
-    r = sigma.shape[0]
+    sig = np.asarray(sigma, dtype=np.float64)
+    r = sig.shape[0]
+    rng = np.random.default_rng(seed)
+    U = torch.from_numpy(orthonormal(rng, m, r)).to(device)
+    V = torch.from_numpy(orthonormal(rng, n, r)).to(device)
+    sigma = torch.from_numpy(sig).to(device)
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
-
-    def orth(rows):
-        G = torch.randn(rows, r, generator=gen, device=device, dtype=torch.float64)
-        Q, R = torch.linalg.qr(G)
-        return Q * torch.sign(torch.diagonal(R))[None, :]
-
-    U = orth(m)
-    V = orth(n)
     A = torch.empty(m, n, device=device, dtype=torch.float32)
     rb = 2048
     for i0 in range(0, m, rb):
