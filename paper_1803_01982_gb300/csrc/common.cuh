@@ -23,6 +23,9 @@ enum CtlSlot : int {
   CTL_BARRIER2 = 10,
   CTL_JACOBI_SWEEPS = 11,
   CTL_NONFINITE = 12,
+  CTL_JAC_PROGRESS = 13,  // Jacobi rounds published to the rotation log
+  CTL_JAC_TOTAL = 14,     // Jacobi total rounds (-1 while running)
+  CTL_SWEEP_ROT0 = 16,  // rotations performed in Jacobi sweeps 0..15 (diagnostic)
   CTL_WORDS = 32,
 };
 
@@ -137,20 +140,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(ctr, 1u);
+    // release: the block's writes (ordered before by bar.sync) become visible
+    // to every block that acquires the counter value
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
     int ok = 1;
     long long spins = 0;
     while (ld_acquire_u32(ctr) < target) {
-      if (*((volatile int *)(ctl + CTL_TIMEOUT)) != 0 || ++spins > spin_limit) {
+      if ((++spins & 63) == 0 &&
+          (*((volatile int *)(ctl + CTL_TIMEOUT)) != 0 || spins > spin_limit)) {
         ok = 0;
         atomicExch(ctl + CTL_TIMEOUT, 1);
         set_status(ctl, STATUS_TIMEOUT);
         break;
       }
-      __nanosleep(20);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -77,8 +77,9 @@ __global__ void transpose_kernel(const T *__restrict__ Src, int64_t lds, int64_t
 // FWD: P upper triangular (forward substitution over columns 0..k-1).
 // !FWD: P lower triangular (backward substitution over columns k-1..0).
 // P(i, j) = Pm[i*psi + j*psj] (so P may be the transpose of a stored matrix).
-// Each row is solved independently by substitution, so each row's result is
-// backward stable: y (P + dP) = x with |dP| <= gamma_k |P|.
+// Each row is solved independently by substitution (multiplying by the
+// rounded reciprocal of each pivot), so each row's result is backward stable:
+// y (P + dP) = x with |dP| <= gamma_{k+1} |P|.
 // A warp solves R rows at a time; lane l owns columns l, l+32, ... (NS slots).
 // ---------------------------------------------------------------------------
 template <typename T, int NS, int R, bool FWD>
@@ -87,10 +88,12 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
                                                         int64_t psi, int64_t psj) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ps = reinterpret_cast<T *>(smem_raw);  // k x k, row-major, P(j, c) at Ps[j*k + c]
+  T *dinv = Ps + (size_t)k * k;             // 1 / P(j, j)
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e / k, j = e - i * k;
     Ps[e] = Pm[(int64_t)i * psi + (int64_t)j * psj];
   }
+  for (int j = threadIdx.x; j < k; j += blockDim.x) dinv[j] = T(1) / Pm[(int64_t)j * psi + (int64_t)j * psj];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t ngroups = (M + R - 1) / R;
@@ -111,10 +114,10 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
         for (int ln = 0; ln < 32; ++ln) {
           const int j = jb * 32 + ln;
           if (j >= k) break;
-          const T d = Ps[j * k + j];
+          const T di = dinv[j];
           T yv[R];
 #pragma unroll
-          for (int r = 0; r < R; ++r) yv[r] = __shfl_sync(0xffffffffu, x[r][jb] / d, ln);
+          for (int r = 0; r < R; ++r) yv[r] = __shfl_sync(0xffffffffu, x[r][jb] * di, ln);
           if (lane == ln) {
 #pragma unroll
             for (int r = 0; r < R; ++r) x[r][jb] = yv[r];
@@ -134,10 +137,10 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
         for (int ln = 31; ln >= 0; --ln) {
           const int j = jb * 32 + ln;
           if (j >= k) continue;
-          const T d = Ps[j * k + j];
+          const T di = dinv[j];
           T yv[R];
 #pragma unroll
-          for (int r = 0; r < R; ++r) yv[r] = __shfl_sync(0xffffffffu, x[r][jb] / d, ln);
+          for (int r = 0; r < R; ++r) yv[r] = __shfl_sync(0xffffffffu, x[r][jb] * di, ln);
           if (lane == ln) {
 #pragma unroll
             for (int r = 0; r < R; ++r) x[r][jb] = yv[r];
@@ -174,31 +177,51 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const T *__restrict__ W,
   T *S = reinterpret_cast<T *>(smem_raw);  // k x k
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) S[e] = W[e];
   __syncthreads();
-  __shared__ T s_d;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // Right-looking, one barrier per step: row j (final after step j-1) stays
+  // unscaled; every thread reads the pivot S(j,j) itself and updates
+  // S(i, c) -= S(j, i) S(j, c) / S(j, j) for j < i <= c.  Rows are scaled by
+  // 1/sqrt(S(j,j)) at the end.
   for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      T d = S[j * k + j];
-      if (!(d > T(0))) {
-        set_status(ctl, STATUS_RANK_DEFICIENT);
-        d = T(1);
+    T d2 = S[j * k + j];
+    if (!(d2 > T(0))) d2 = T(1);
+    const T inv = T(1) / d2;
+    if (sizeof(T) == 4 && (k & 3) == 0) {
+      // 16-byte vectors from the aligned column at or below j+1; entries left
+      // of the diagonal (lower triangle) are never read, so updating them is
+      // harmless
+      const int c4_0 = (j + 1) >> 2, n4 = k >> 2;
+      float4 *S4 = reinterpret_cast<float4 *>(S);
+      for (int i = j + 1 + wid; i < k; i += nwarp) {
+        const float sji = (float)(S[j * k + i] * inv);
+        for (int c4 = c4_0 + lane; c4 < n4; c4 += 32) {
+          const float4 a = S4[(j * k >> 2) + c4];
+          float4 b = S4[(i * k >> 2) + c4];
+          b.x = fmaf(-sji, a.x, b.x);
+          b.y = fmaf(-sji, a.y, b.y);
+          b.z = fmaf(-sji, a.z, b.z);
+          b.w = fmaf(-sji, a.w, b.w);
+          S4[(i * k >> 2) + c4] = b;
+        }
       }
-      s_d = sqrt(d);
-    }
-    __syncthreads();
-    const T d = s_d;
-    for (int c = j + threadIdx.x; c < k; c += blockDim.x) S[j * k + c] = (c == j) ? d : S[j * k + c] / d;
-    __syncthreads();
-    // trailing update of the upper triangle: S(i, c) -= R(j, i) R(j, c), j < i <= c
-    const int rem = k - j - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int i = j + 1 + e / rem, c = j + 1 + e % rem;
-      if (c >= i) S[i * k + c] = fma(-S[j * k + i], S[j * k + c], S[i * k + c]);
+    } else {
+      for (int i = j + 1 + wid; i < k; i += nwarp) {
+        const T sji = S[j * k + i] * inv;
+        for (int c = i + lane; c < k; c += 32) S[i * k + c] = fma(-sji, S[j * k + c], S[i * k + c]);
+      }
     }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int i = e / k, c = e - i * k;
-    R[e] = (c >= i) ? S[e] : T(0);
+    T d2 = S[i * k + i];
+    const bool bad = !(d2 > T(0));
+    if (bad) {
+      if (c == i) set_status(ctl, STATUS_RANK_DEFICIENT);
+      d2 = T(1);
+    }
+    const T rd = sqrt(d2);
+    R[e] = (c > i) ? S[e] / rd : ((c == i) ? rd : T(0));
   }
 }
 
@@ -508,6 +531,8 @@ __global__ void init_ctl_kernel(int *ctl, double *dctl) {
     dctl[D_G2_FIRST] = 1.0;
     ctl[CTL_CAND_FIRST] = -1;
     ctl[CTL_CAND] = 0x7fffffff;
+    ctl[CTL_JAC_PROGRESS] = 0;
+    ctl[CTL_JAC_TOTAL] = -1;
   }
 }
 

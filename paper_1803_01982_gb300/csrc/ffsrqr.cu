@@ -90,6 +90,7 @@ struct ffsrqr_plan_s {
       off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
       off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_part, off_sgnv, off_sgni, off_sgn;
   size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
+  size_t off_jlog;                            // Jacobi rotation log
   size_t part_cap;  // elements of the split-K buffer
   int qrcp_grid, qrcp_threads;
   int smem_optin;  // max dynamic shared memory per block (bytes)
@@ -273,14 +274,19 @@ template <typename T, bool FWD>
 int launch_trsm(cudaStream_t st, const ffsrqr_plan_s *P, T *X, int64_t ldx, int64_t M, const T *Pm,
                 int64_t psi, int64_t psj) {
   const int k = P->k;
-  const size_t smem = (size_t)k * k * sizeof(T);
+  const size_t smem = (size_t)k * (k + 1) * sizeof(T);
   const int threads = 512;
-  const int64_t groups = cdiv(M, 4);
+  // rows per warp: many rows -> 8 (FP32) / 4 (FP64) for reuse of each pivot
+  // row; few rows (a k x k inverse) -> 1, to spread them over more warps
+  const bool few = M < 4096;
+  const int rr = few ? 1 : ((sizeof(T) == 4) ? 8 : 4);
+  const int64_t groups = cdiv(M, rr);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(groups, threads / 32), P->num_sms));
   const int ns = (int)cdiv(k, 32);
 #define TRSM_CASE(NSv)                                                                        \
   if (ns <= NSv) {                                                                            \
-    auto fn = trsm_rows_kernel<T, NSv, 4, FWD>;                                               \
+    auto fn = few ? trsm_rows_kernel<T, NSv, 1, FWD>                                          \
+                  : trsm_rows_kernel<T, NSv, (sizeof(T) == 4) ? 8 : 4, FWD>;                  \
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
     fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj);                              \
     CKL("trsm_rows");                                                                         \
@@ -569,12 +575,13 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   MARK(10);
   {
     const int kk = k + (k & 1);
-    const size_t smem = (size_t)kk * k * sizeof(T) + (size_t)(2 * kk + kk) * sizeof(T) +
-                        (size_t)(kk + 4) * sizeof(int) + 64;
+    const int kp = (int)round_up(k, 16 / (int)sizeof(T));
+    const size_t smem = (size_t)kk * kp * sizeof(T) + (size_t)kk * sizeof(T) + (size_t)kk * sizeof(int) + 64;
     CK(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const T eps = (sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16);
     const T tol = (sizeof(T) == 4) ? T(4) * sqrt(T(k)) * eps : T(k) * eps;
-    jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, w.ctl, 40, tol);
+    T *jlog = reinterpret_cast<T *>(ws + P->off_jlog);
+    jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, jlog, w.ctl, JAC_MAX_SWEEPS, tol);
     CKL("jacobi_svd");
   }
   MARK(11);
@@ -651,6 +658,10 @@ void layout(ffsrqr_plan_s *P) {
   P->off_mt = take((size_t)k * k * E);
   P->off_us = take((size_t)k * k * E);
   P->off_vs = take((size_t)k * k * E);
+  {
+    const int kk = k + (k & 1);
+    P->off_jlog = take((size_t)JAC_MAX_SWEEPS * (kk - 1) * (kk / 2) * 2 * E);  // Jacobi rotation log
+  }
   P->nblk_sign = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max(m, n), 64), nsm));
   P->off_sgnv = take((size_t)P->nblk_sign * k * E);
   P->off_sgni = take((size_t)P->nblk_sign * k * sizeof(int));
@@ -807,9 +818,10 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
 
 int ffsrqr_destroy(ffsrqr_plan_t plan) {
   if (!plan) return -1;
-  if (plan->ev_ok)
+  if (plan->ev_ok) {
     for (int i = 0; i < 13; ++i) cudaEventDestroy(plan->ev[i]);
     for (int i = 0; i < 6; ++i) cudaEventDestroy(plan->ev_tc[i / 2][i % 2]);
+  }
   delete plan;
   return 0;
 }

@@ -148,16 +148,16 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
         }
         s_tau = tau;
         s_beta = beta;
-        if (b == 0) {
-          a.piv[j] = wi;
-          for (int t = 0; t < j; ++t) a.S11[(size_t)t * a.k + j] = v[t];
-          a.S11[(size_t)j * a.k + j] = beta;
-          for (int t = j + 1; t < a.k; ++t) a.S11[(size_t)t * a.k + j] = T(0);
-        }
+        if (b == 0) a.piv[j] = wi;
         a.sel[wi] = 1;
       }
       __syncthreads();
       const T tau = s_tau, beta = s_beta;
+      if (b == 0) {
+        // column j of S11: transformed pivot column above the diagonal, beta, zeros
+        for (int t = threadIdx.x; t < a.k; t += blockDim.x)
+          a.S11[(size_t)t * a.k + j] = (t < j) ? v[t] : ((t == j) ? beta : T(0));
+      }
       if (tau != T(0)) {
         const T scal = T(1) / (v[j] - beta);
         for (int t = j + 1 + threadIdx.x; t < s; t += blockDim.x) v[t] *= scal;
