@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
     if (FWD) {
 #pragma unroll
       for (int jb = 0; jb < NS; ++jb) {
+#pragma unroll 1
         for (int ln = 0; ln < 32; ++ln) {
           const int j = jb * 32 + ln;
           if (j >= k) break;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
     } else {
 #pragma unroll
       for (int jb = NS - 1; jb >= 0; --jb) {
+#pragma unroll 1
         for (int ln = 31; ln >= 0; --ln) {
           const int j = jb * 32 + ln;
           if (j >= k) continue;
@@ -169,59 +171,197 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
 // Cholesky  W = R^T R  (one block; W symmetric k x k, only its upper triangle
 // is read).  R is written upper triangular (k x k, zero below).  A non-positive
 // pivot marks the status RANK_DEFICIENT and continues with a unit pivot.
+//
+// Blocked right-looking factorisation in shared memory with 8-column steps:
+//   1. one thread factors the 8 x 8 diagonal block and inverts its factor,
+//      X = R_dd^{-1}, entirely in registers (no shuffles or barriers on the
+//      sequential chain of pivots);
+//   2. the panel R12 = R_dd^{-T} S12 = X^T S12, one thread per column;
+//   3. the symmetric rank-8 update S22 -= R12^T R12 of the upper triangle in
+//      4 x 4 register tiles (upper-triangle tiles only).
+// The diagonal blocks are at least as well conditioned as R, so multiplying
+// by their explicit inverses keeps FP32 accuracy for the Gram matrices this
+// library factors.
 // ---------------------------------------------------------------------------
+constexpr int CHOL_NB = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(1024) cholesky_kernel(const T *__restrict__ W, int k,
-                                                        T *__restrict__ R, int *ctl) {
+__global__ void __launch_bounds__(512, 1) cholesky_kernel(const T *__restrict__ W, int k,
+                                                          T *__restrict__ R, int *ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *S = reinterpret_cast<T *>(smem_raw);  // k x k
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) S[e] = W[e];
+  T *S = reinterpret_cast<T *>(smem_raw);  // k x k, row-major; becomes R in place
+  __shared__ T Xs[CHOL_NB][CHOL_NB];         // X = R_dd^{-1}, Xs[j][t] = X(j, t)
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool vec = (sizeof(T) == 4) && ((k & 3) == 0) && (((uintptr_t)W & 15) == 0) && (((uintptr_t)R & 15) == 0);
+  if (vec) {
+    const float4 *W4 = reinterpret_cast<const float4 *>(W);
+    float4 *S4 = reinterpret_cast<float4 *>(S);
+#pragma unroll 4
+    for (int e = tid; e < (k * k) >> 2; e += nthr) S4[e] = W4[e];
+  } else {
+#pragma unroll 4
+    for (int e = tid; e < k * k; e += nthr) S[e] = W[e];
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  // Right-looking, one barrier per step: row j (final after step j-1) stays
-  // unscaled; every thread reads the pivot S(j,j) itself and updates
-  // S(i, c) -= S(j, i) S(j, c) / S(j, j) for j < i <= c.  Rows are scaled by
-  // 1/sqrt(S(j,j)) at the end.
-  for (int j = 0; j < k; ++j) {
-    T d2 = S[j * k + j];
-    if (!(d2 > T(0))) d2 = T(1);
-    const T inv = T(1) / d2;
-    if (sizeof(T) == 4 && (k & 3) == 0) {
-      // 16-byte vectors from the aligned column at or below j+1; entries left
-      // of the diagonal (lower triangle) are never read, so updating them is
-      // harmless
-      const int c4_0 = (j + 1) >> 2, n4 = k >> 2;
-      float4 *S4 = reinterpret_cast<float4 *>(S);
-      for (int i = j + 1 + wid; i < k; i += nwarp) {
-        const float sji = (float)(S[j * k + i] * inv);
-        for (int c4 = c4_0 + lane; c4 < n4; c4 += 32) {
-          const float4 a = S4[(j * k >> 2) + c4];
-          float4 b = S4[(i * k >> 2) + c4];
-          b.x = fmaf(-sji, a.x, b.x);
-          b.y = fmaf(-sji, a.y, b.y);
-          b.z = fmaf(-sji, a.z, b.z);
-          b.w = fmaf(-sji, a.w, b.w);
-          S4[(i * k >> 2) + c4] = b;
+  for (int jb = 0; jb < k; jb += CHOL_NB) {
+    const int nb = min(CHOL_NB, k - jb);
+    // 1. diagonal block (padded with the identity beyond nb)
+    if (tid == 0) {
+      T a[CHOL_NB][CHOL_NB];
+#pragma unroll
+      for (int r = 0; r < CHOL_NB; ++r)
+#pragma unroll
+        for (int c = 0; c < CHOL_NB; ++c)
+          a[r][c] = (r <= c && c < nb) ? S[(jb + r) * k + jb + c] : ((r == c) ? T(1) : T(0));
+      bool bad = false;
+#pragma unroll
+      for (int r = 0; r < CHOL_NB; ++r) {
+        T d = a[r][r];
+        if (!(d > T(0))) {
+          bad = true;
+          d = T(1);
+        }
+        const T sd = sqrt(d);
+        const T inv = T(1) / sd;
+        a[r][r] = sd;
+#pragma unroll
+        for (int c = r + 1; c < CHOL_NB; ++c) a[r][c] *= inv;
+#pragma unroll
+        for (int i = r + 1; i < CHOL_NB; ++i)
+#pragma unroll
+          for (int c = i; c < CHOL_NB; ++c) a[i][c] = fma(-a[r][i], a[r][c], a[i][c]);
+      }
+      if (bad) set_status(ctl, STATUS_RANK_DEFICIENT);
+#pragma unroll
+      for (int r = 0; r < CHOL_NB; ++r)
+#pragma unroll
+        for (int c = r; c < CHOL_NB; ++c)
+          if (c < nb) S[(jb + r) * k + jb + c] = a[r][c];
+      // X = R_dd^{-1} by back substitution, column by column
+      T rinv[CHOL_NB];
+#pragma unroll
+      for (int r = 0; r < CHOL_NB; ++r) rinv[r] = T(1) / a[r][r];
+#pragma unroll
+      for (int c = 0; c < CHOL_NB; ++c) {
+        T x[CHOL_NB];
+#pragma unroll
+        for (int r = CHOL_NB - 1; r >= 0; --r) {
+          if (r > c) {
+            x[r] = T(0);
+          } else {
+            T acc = (r == c) ? T(1) : T(0);
+#pragma unroll
+            for (int j = r + 1; j <= c; ++j) acc = fma(-a[r][j], x[j], acc);
+            x[r] = acc * rinv[r];
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < CHOL_NB; ++r) Xs[r][c] = x[r];
+      }
+    }
+    __syncthreads();
+    const int t0 = jb + nb;  // first trailing column
+    const int nt = k - t0;
+    if (nt <= 0) break;
+    // 2. panel R12(t, c) = sum_{j <= t} X(j, t) S12(j, c), one thread per column
+    for (int c = t0 + tid; c < k; c += nthr) {
+      T sv[CHOL_NB];
+#pragma unroll
+      for (int j = 0; j < CHOL_NB; ++j) sv[j] = (j < nb) ? S[(jb + j) * k + c] : T(0);
+#pragma unroll
+      for (int t = 0; t < CHOL_NB; ++t) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j <= t; ++j) acc = fma(Xs[j][t], sv[j], acc);
+        if (t < nb) S[(jb + t) * k + c] = acc;
+      }
+    }
+    __syncthreads();
+    // 3. trailing update S(i, c) -= sum_t R(t, i) R(t, c), t0 <= i <= c < k,
+    //    over the upper-triangle 4 x 4 tiles (ti <= tc).  e -> (a, b), b <= a,
+    //    by the triangular-number inverse, then ti = nt4 - 1 - a, tc = ti + b:
+    //    consecutive threads take consecutive column tiles of one tile row,
+    //    so their shared-memory rows are contiguous (no bank conflicts).
+    //    Entries below the diagonal inside diagonal tiles are updated too;
+    //    the lower triangle is never read.
+    const int nt4 = (nt + 3) >> 2;
+    const int ntiles = nt4 * (nt4 + 1) / 2;
+    const bool v4 = (sizeof(T) == 4) && ((k & 3) == 0) && ((t0 & 3) == 0);
+    for (int e = tid; e < ntiles; e += nthr) {
+      int a = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (a * (a + 1) / 2 > e) --a;
+      while ((a + 1) * (a + 2) / 2 <= e) ++a;
+      const int ti = nt4 - 1 - a, tc = ti + (e - a * (a + 1) / 2);
+      const int i0 = t0 + 4 * ti, c0 = t0 + 4 * tc;
+      T acc[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[q][u] = T(0);
+#pragma unroll
+      for (int t = 0; t < CHOL_NB; ++t) {
+        if (t < nb) {
+          const T *row = S + (jb + t) * k;
+          T av[4], bv[4];
+          if (v4) {
+            const float4 fa = *reinterpret_cast<const float4 *>(row + i0);
+            const float4 fb = *reinterpret_cast<const float4 *>(row + c0);
+            av[0] = fa.x; av[1] = fa.y; av[2] = fa.z; av[3] = fa.w;
+            bv[0] = fb.x; bv[1] = fb.y; bv[2] = fb.z; bv[3] = fb.w;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              av[q] = (i0 + q < k) ? row[i0 + q] : T(0);
+              bv[q] = (c0 + q < k) ? row[c0 + q] : T(0);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[q][u] = fma(av[q], bv[u], acc[q][u]);
         }
       }
-    } else {
-      for (int i = j + 1 + wid; i < k; i += nwarp) {
-        const T sji = S[j * k + i] * inv;
-        for (int c = i + lane; c < k; c += 32) S[i * k + c] = fma(-sji, S[j * k + c], S[i * k + c]);
+      if (v4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (i0 + q < k) {
+            float4 *p4 = reinterpret_cast<float4 *>(S + (i0 + q) * k + c0);
+            float4 v = *p4;
+            v.x -= (float)acc[q][0];
+            v.y -= (float)acc[q][1];
+            v.z -= (float)acc[q][2];
+            v.w -= (float)acc[q][3];
+            *p4 = v;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + q < k && c0 + u < k && c0 + u >= i0 + q) S[(i0 + q) * k + c0 + u] -= acc[q][u];
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e / k, c = e - i * k;
-    T d2 = S[i * k + i];
-    const bool bad = !(d2 > T(0));
-    if (bad) {
-      if (c == i) set_status(ctl, STATUS_RANK_DEFICIENT);
-      d2 = T(1);
+  if (vec) {
+    float4 *R4 = reinterpret_cast<float4 *>(R);
+    const float4 *S4 = reinterpret_cast<const float4 *>(S);
+    const int k4 = k >> 2;
+    for (int e = tid; e < k * k4; e += nthr) {
+      const int i = e / k4, c = (e - i * k4) * 4;
+      float4 v = S4[e];
+      if (c + 0 < i) v.x = 0.f;
+      if (c + 1 < i) v.y = 0.f;
+      if (c + 2 < i) v.z = 0.f;
+      if (c + 3 < i) v.w = 0.f;
+      R4[e] = v;
     }
-    const T rd = sqrt(d2);
-    R[e] = (c > i) ? S[e] / rd : ((c == i) ? rd : T(0));
+  } else {
+    for (int e = tid; e < k * k; e += nthr) {
+      const int i = e / k, c = e - i * k;
+      R[e] = (c >= i) ? S[e] : T(0);
+    }
   }
 }
 
@@ -538,9 +678,11 @@ __global__ void init_ctl_kernel(int *ctl, double *dctl) {
 
 // Identity (k x k).
 template <typename T>
-__global__ void eye_kernel(T *__restrict__ X, int k) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x)
-    X[e] = ((e / k) == (e % k)) ? T(1) : T(0);
+__global__ void eye_kernel(T *__restrict__ X, int k, int64_t ld) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    X[i * ld + j] = (i == j) ? T(1) : T(0);
+  }
 }
 
 // Non-finite scan of A (sets status NONFINITE).

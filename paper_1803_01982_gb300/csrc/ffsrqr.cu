@@ -90,6 +90,7 @@ struct ffsrqr_plan_s {
       off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
       off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_part, off_sgnv, off_sgni, off_sgn;
   size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
+  size_t off_sinv, off_sh, off_sl, off_scr;   // tensor-core small products (FFSRQR_MIXED)
   size_t off_jlog;                            // Jacobi rotation log
   size_t part_cap;  // elements of the split-K buffer
   int qrcp_grid, qrcp_threads;
@@ -124,7 +125,9 @@ int launch_gemm(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int 
   if (M <= 0 || N <= 0) return 0;
   T *part = reinterpret_cast<T *>(ws + P->off_part);
   const bool wide = N > 64;
-  const int BM = 64, BN = wide ? 128 : 64;
+  // small products (k x k factors): 32 x 32 tiles so that more blocks run
+  const bool small = cdiv(M, 64) * cdiv(N, 64) < P->num_sms / 2 && K < 512;
+  const int BM = small ? 32 : 64, BN = small ? 32 : (wide ? 128 : 64);
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   int splits = 1;
   if (tiles < 2 * P->num_sms && K >= 512) {
@@ -139,7 +142,10 @@ int launch_gemm(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int 
   dim3 grid((unsigned)cdiv(M, BM), (unsigned)cdiv(N, BN), (unsigned)splits);
 #define GEMM_CASE(XMv, YNv)                                                                        \
   if (XM == XMv && YN == YNv) {                                                                    \
-    if (wide)                                                                                      \
+    if (small)                                                                                     \
+      gemm_simt_kernel<T, 32, 32, 16, 2, 2, XMv, YNv>                                              \
+          <<<grid, 256, 0, st>>>(M, N, K, X, ldx, Y, ldy, C, ldc, klen, part, alpha, beta);        \
+    else if (wide)                                                                                 \
       gemm_simt_kernel<T, 64, 128, 8, 4, 8, XMv, YNv>                                              \
           <<<grid, 256, 0, st>>>(M, N, K, X, ldx, Y, ldy, C, ldc, klen, part, alpha, beta);        \
     else                                                                                           \
@@ -210,11 +216,13 @@ bool make_map(CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, 
 // A: the big matrix (row-major, lda), A_MN selects the contraction over its
 // rows (passes 1, 2) or its columns (pass 3).  Bt / Btl: thin operand (and its
 // TF32 tail for nprod = 3) stored N x K row-major with leading dim ldb.
+// pass 0..2 records the pass-kernel events; -1 for the other products.
 int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pass, int nprod, bool a_mn, int M,
               int N, int K, const float *A, int64_t lda, const float *Bt, const float *Btl, int64_t ldb,
               float *C, int64_t ldc) {
   const int BK = (nprod == 1) ? 32 : 16;
   const int ntile = (int)round_up(N, 16);
+  if (ntile > TC_MAX_NT) return FFSRQR_STATUS_UNSUPPORTED;
   CUtensorMap mA, mB, mBl;
   if (a_mn) {
     // A^T tile: inner = A's column index (M), outer = A's row index (K)
@@ -231,12 +239,15 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   sc.KB = (int)cdiv(K, BK);
   sc.tiles = (int)cdiv(M, TC_BM);
   sc.U = (long long)sc.tiles * sc.KB;
-  sc.G = (int)std::min<long long>(P->num_sms, sc.U);
+  sc.G = (int)std::min<long long>(std::min(P->num_sms, TC_MAX_GRID), sc.U);
   sc.ntile = ntile;
   sc.ldc = ldc;
   sc.C = C;
   sc.part = reinterpret_cast<float *>(ws + P->off_tcpart);
   sc.ctl = reinterpret_cast<int *>(ws + P->off_ctl);
+  sc.vec4 = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0);
+  // few tiles shared by many blocks (a Gram): one row per fixup block
+  sc.fix_rows = (8LL * sc.tiles < sc.G) ? 1 : 4;
   int stage_bytes = 0;
   if (nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true>::bytes(ntile);
   else if (nprod == 3 && a_mn) stage_bytes = TcStage<16, 3, true>::bytes(ntile);
@@ -249,9 +260,9 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   {                                                                                                  \
     auto fn = tc_gemm_kernel<BKv, NPv, AMNv>;                                                        \
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));            \
-    if (P->ev_ok) cudaEventRecord(P->ev_tc[pass][0], st);                                            \
+    if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[pass][0], st);                               \
     fn<<<sc.G, TC_THREADS, smem, st>>>(mA, mB, mBl, sc);                                             \
-    if (P->ev_ok) cudaEventRecord(P->ev_tc[pass][1], st);                                            \
+    if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[pass][1], st);                               \
   }
   if (nprod == 1 && a_mn) TC_LAUNCH(32, 1, true)
   else if (nprod == 3 && a_mn) TC_LAUNCH(16, 3, true)
@@ -259,7 +270,7 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   else return FFSRQR_STATUS_UNSUPPORTED;
 #undef TC_LAUNCH
   CKL("tc_gemm");
-  tc_fixup_kernel<<<dim3(sc.tiles, TC_BM / 32), 256, 0, st>>>(sc);
+  tc_fixup_kernel<<<dim3(sc.tiles, TC_BM / sc.fix_rows), 256, 0, st>>>(sc);
   CKL("tc_fixup");
   return 0;
 }
@@ -305,7 +316,7 @@ int launch_chol(cudaStream_t st, const ffsrqr_plan_s *P, const T *W, T *R, int *
   const int k = P->k;
   const size_t smem = (size_t)k * k * sizeof(T);
   CK(cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  cholesky_kernel<T><<<1, 1024, smem, st>>>(W, k, R, ctl);
+  cholesky_kernel<T><<<1, 512, smem, st>>>(W, k, R, ctl);
   CKL("cholesky");
   return 0;
 }
@@ -420,7 +431,9 @@ int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A,
 
 template <typename T>
 bool use_tc(const ffsrqr_plan_s *P, const T *A, int64_t lda) {
-  return sizeof(T) == 4 && P->mode == FFSRQR_MIXED && tc_ok(A, lda);
+  // the tensor-core epilogue holds N tiles of up to TC_MAX_NT columns (the
+  // sketch has s columns); wider problems run the CUDA-core passes
+  return sizeof(T) == 4 && P->mode == FFSRQR_MIXED && tc_ok(A, lda) && round_up(P->s, 16) <= TC_MAX_NT;
 }
 
 // Pass 2 (a_mn: G^T = A^T X, X = Q1 with rows = m) or pass 3 (tmp = A X,
@@ -441,6 +454,100 @@ int tc_thin_pass(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, boo
   CKL("split_tf32");
   const int M = (int)(a_mn ? P->n : P->m);
   return launch_tc(st, P, ws, a_mn ? 1 : 2, 3, a_mn, M, k, (int)rows, A, lda, bh, bl, ldt, C, P->ldk);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core dense products of the mixed mode (3xTF32: FP32-level accuracy)
+// ---------------------------------------------------------------------------
+struct TcBufs {
+  float *bh, *bl;    // K-major split of a tall operand (k x max(m, n))
+  float *sinv;       // k x k (ld ldk): (R^{-1})^T
+  float *sh, *sl;    // split of a small operand (<= 256 x k, ld ldk)
+  float *scr;        // max(m, n) x k (ld ldk) scratch
+};
+
+TcBufs tc_bufs(const ffsrqr_plan_s *P, unsigned char *ws) {
+  TcBufs b;
+  b.bh = reinterpret_cast<float *>(ws + P->off_bh);
+  b.bl = reinterpret_cast<float *>(ws + P->off_bl);
+  b.sinv = reinterpret_cast<float *>(ws + P->off_sinv);
+  b.sh = reinterpret_cast<float *>(ws + P->off_sh);
+  b.sl = reinterpret_cast<float *>(ws + P->off_sl);
+  b.scr = reinterpret_cast<float *>(ws + P->off_scr);
+  return b;
+}
+
+// Dh / Dl (cols x rows, ld ldd) = TF32 head / tail of Src^T (Src rows x cols).
+int tc_split_t(cudaStream_t st, const float *Src, int64_t lds, int64_t rows, int64_t cols, float *Dh,
+               float *Dl, int64_t ldd) {
+  transpose_split_kernel<<<dim3((unsigned)cdiv(rows, 32), (unsigned)cdiv(cols, 32)), dim3(32, 8), 0, st>>>(
+      Src, lds, rows, cols, Dh, Dl, ldd);
+  CKL("transpose_split");
+  return 0;
+}
+
+// W (k x k) = X^T X for X rows x k (ld ldx, 16-byte aligned rows).
+int tc_gram(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const float *X, int64_t ldx,
+            int64_t rows, float *W) {
+  const int k = P->k;
+  const TcBufs b = tc_bufs(P, ws);
+  const int64_t ldt = round_up(rows, 4);
+  int rc;
+  if ((rc = tc_split_t(st, X, ldx, rows, k, b.bh, b.bl, ldt))) return rc;
+  return launch_tc(st, P, ws, -1, 3, true, k, k, (int)rows, X, ldx, b.bh, b.bl, ldt, W, k);
+}
+
+// sh / sl = split of (R^{-1})^T for an upper-triangular R (k x k, ld k): the
+// K-major operand of the product X R^{-1}.  The inverse is formed by the
+// row-wise triangular solve on the identity.
+int tc_inv_t(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const float *R) {
+  const int k = P->k;
+  const TcBufs b = tc_bufs(P, ws);
+  int rc;
+  eye_kernel<float><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(b.sinv, k, P->ldk);
+  CKL("eye");
+  if ((rc = launch_trsm<float, false>(st, P, b.sinv, P->ldk, k, R, 1, k))) return rc;
+  split_tf32_kernel<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(b.sinv, P->ldk, k, k, b.sh, b.sl);
+  CKL("split_tf32");
+  return 0;
+}
+
+// C (rows x N, ldc) = X (rows x K, ldx) Op, with Op's K-major split (N x K,
+// ld ldk) already in sh / sl.
+int tc_mul(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const float *X, int64_t ldx,
+           int64_t rows, int N, int K, float *C, int64_t ldc) {
+  const TcBufs b = tc_bufs(P, ws);
+  return launch_tc(st, P, ws, -1, 3, false, (int)rows, N, K, X, ldx, b.sh, b.sl, P->ldk, C, ldc);
+}
+
+// CholeskyQR2 on the tensor cores: Q (rows x k, ld ldk) = X R^{-1}, R = R2 R1
+// (Rout, optional).  Each sweep forms the Gram X^T X, its Cholesky factor, the
+// explicit inverse of the factor and the product; X is first brought to a
+// small condition number by the caller, so the explicit inverse is accurate.
+// Q may alias X.
+int cholqr2_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const float *X, int64_t rows,
+               float *Q, float *Rout) {
+  const int k = P->k;
+  const int64_t ldk = P->ldk;
+  const TcBufs b = tc_bufs(P, ws);
+  float *W = reinterpret_cast<float *>(ws + P->off_w);
+  float *R1 = reinterpret_cast<float *>(ws + P->off_rc1);
+  float *R2 = reinterpret_cast<float *>(ws + P->off_rc2);
+  int *ctl = reinterpret_cast<int *>(ws + P->off_ctl);
+  int rc;
+  if ((rc = tc_gram(st, P, ws, X, ldk, rows, W))) return rc;
+  if ((rc = launch_chol<float>(st, P, W, R1, ctl))) return rc;
+  if ((rc = tc_inv_t(st, P, ws, R1))) return rc;
+  if ((rc = tc_mul(st, P, ws, X, ldk, rows, k, k, b.scr, ldk))) return rc;
+  if ((rc = tc_gram(st, P, ws, b.scr, ldk, rows, W))) return rc;
+  if ((rc = launch_chol<float>(st, P, W, R2, ctl))) return rc;
+  if ((rc = tc_inv_t(st, P, ws, R2))) return rc;
+  if ((rc = tc_mul(st, P, ws, b.scr, ldk, rows, k, k, Q, ldk))) return rc;
+  if (Rout) {
+    trmm_upper_kernel<float><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(R2, R1, k, Rout);
+    CKL("trmm_upper");
+  }
+  return 0;
 }
 
 template <typename T>
@@ -515,7 +622,11 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
       A, lda, m, k, piv, w.q1, ldk);
   CKL("gather_cols");
   if ((rc = launch_trsm<T, true>(st, P, w.q1, ldk, m, w.s11, k, 1))) return rc;
-  if ((rc = cholqr2<T>(st, P, ws, w.q1, ldk, m, nullptr))) return rc;
+  if (tc) {
+    if ((rc = cholqr2_tc(st, P, ws, (const float *)w.q1, m, (float *)w.q1, nullptr))) return rc;
+  } else if ((rc = cholqr2<T>(st, P, ws, w.q1, ldk, m, nullptr))) {
+    return rc;
+  }
   MARK(4);
   // a5: pass 2, G^T (n x k) = A^T Q1
   if (tc) {
@@ -528,7 +639,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   // a6: R11, R11^{-1}, Z^T = G^T R11^{-T}
   extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11);
   CKL("extract_r11");
-  eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k);
+  eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k, k);
   CKL("eye");
   if ((rc = launch_trsm<T, true>(st, P, w.rinv, k, k, w.r11, k, 1))) return rc;
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, w.zt,
@@ -539,8 +650,13 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   gather_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * s, 256), 256, 0, st>>>(w.bt, lds, k, s, piv, w.bjt,
                                                                              lds);
   CKL("gather_rows");
-  if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, k, w.zt, ldk, false, w.bjt, lds, true, w.cbt, lds)))
+  if (tc) {
+    const TcBufs tb = tc_bufs(P, ws);
+    if ((rc = tc_split_t(st, (const float *)w.bjt, lds, k, s, tb.sh, tb.sl, ldk))) return rc;
+    if ((rc = tc_mul(st, P, ws, (const float *)w.zt, ldk, n, s, k, (float *)w.cbt, lds))) return rc;
+  } else if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, k, w.zt, ldk, false, w.bjt, lds, true, w.cbt, lds))) {
     return rc;
+  }
   trailing_norms_kernel<T><<<P->nblk_tn, 256, 0, st>>>(w.bt, w.cbt, lds, n, s, w.sel, w.r, w.bv, w.bi);
   CKL("trailing_norms");
   if (k < n) {
@@ -550,10 +666,14 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   // a7: swap loop (Alg. 4) runs here when g2 > g
   MARK(7);
   // a8: V' = orth(Z^T), R_z
-  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.zt, ldk, w.vp,
-                                                                                          ldk, n, k);
-  CKL("copy_vp");
-  if ((rc = cholqr2<T>(st, P, ws, w.vp, ldk, n, w.rz))) return rc;
+  if (tc) {
+    if ((rc = cholqr2_tc(st, P, ws, (const float *)w.zt, n, (float *)w.vp, (float *)w.rz))) return rc;
+  } else {
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.zt, ldk, w.vp,
+                                                                                            ldk, n, k);
+    CKL("copy_vp");
+    if ((rc = cholqr2<T>(st, P, ws, w.vp, ldk, n, w.rz))) return rc;
+  }
   MARK(8);
   // a9: pass 3, tmp (m x k) = A V'
   if (tc) {
@@ -569,7 +689,11 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   CKL("copy_yt");
   if ((rc = launch_trsm<T, false>(st, P, w.yt, ldk, m, w.rz, 1, k))) return rc;
   if ((rc = launch_trsm<T, true>(st, P, w.yt, ldk, m, w.r11, k, 1))) return rc;
-  if ((rc = cholqr2<T>(st, P, ws, w.yt, ldk, m, w.rt))) return rc;
+  if (tc) {
+    if ((rc = cholqr2_tc(st, P, ws, (const float *)w.yt, m, (float *)w.yt, (float *)w.rt))) return rc;
+  } else if ((rc = cholqr2<T>(st, P, ws, w.yt, ldk, m, w.rt))) {
+    return rc;
+  }
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.rt, k, false, w.r11, k, true, w.t1, k))) return rc;
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.t1, k, false, w.rz, k, false, w.mt, k))) return rc;
   MARK(10);
@@ -586,8 +710,16 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   }
   MARK(11);
   // a11: U = Q_t U_s, V = V' V_s, sign rule
-  if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, k, w.yt, ldk, false, w.us, k, true, U, ldu))) return rc;
-  if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, k, w.vp, ldk, false, w.vs, k, true, V, ldv))) return rc;
+  if (tc) {
+    const TcBufs tb = tc_bufs(P, ws);
+    if ((rc = tc_split_t(st, (const float *)w.us, k, k, k, tb.sh, tb.sl, ldk))) return rc;
+    if ((rc = tc_mul(st, P, ws, (const float *)w.yt, ldk, m, k, k, (float *)U, ldu))) return rc;
+    if ((rc = tc_split_t(st, (const float *)w.vs, k, k, k, tb.sh, tb.sl, ldk))) return rc;
+    if ((rc = tc_mul(st, P, ws, (const float *)w.vp, ldk, n, k, k, (float *)V, ldv))) return rc;
+  } else {
+    if ((rc = launch_gemm<T>(st, P, ws, (int)m, k, k, w.yt, ldk, false, w.us, k, true, U, ldu))) return rc;
+    if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, k, w.vp, ldk, false, w.vs, k, true, V, ldv))) return rc;
+  }
   sign_partial_kernel<T><<<P->nblk_sign, 256, 0, st>>>(U, ldu, m, k, w.sgnv, w.sgni);
   CKL("sign_partial");
   sign_final_kernel<T><<<(unsigned)cdiv(k, 256), 256, 0, st>>>(U, ldu, k, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
@@ -674,8 +806,13 @@ void layout(ffsrqr_plan_s *P) {
     P->off_tt = take((size_t)k * ldmax * sizeof(float));
     P->off_bh = take((size_t)k * ldmax * sizeof(float));
     P->off_bl = take((size_t)k * ldmax * sizeof(float));
+    P->off_sinv = take((size_t)k * ldk * sizeof(float));
+    P->off_sh = take((size_t)256 * ldk * sizeof(float));
+    P->off_sl = take((size_t)256 * ldk * sizeof(float));
+    P->off_scr = take((size_t)std::max(m, n) * ldk * sizeof(float));
   } else {
     P->off_tcpart = P->off_tt = P->off_bh = P->off_bl = 0;
+    P->off_sinv = P->off_sh = P->off_sl = P->off_scr = 0;
   }
   P->ws_bytes = off;
   auto item = [&](int i, size_t o, int64_t r, int64_t c, int64_t ld) {

@@ -25,9 +25,20 @@
 // Ah / Al on the way when NPROD = 3); for pass 3 the TMA lands A K-major and
 // the converters only split it in place.
 //
-// Warp roles (12 warps): 0 = TMA producer, 1 = MMA issuer (one thread), 2 =
-// TMEM allocation owner, 3 = idle, 4..7 = epilogue (TMEM -> registers ->
-// global; warp w reads TMEM lanes 32*(w%4)..+31), 8..11 = converters.
+// Accumulation: the tensor core adds each MMA's products into the FP32 TMEM
+// accumulator without round-to-nearest (the sum is biased toward zero by up
+// to one unit in the last place per MMA), which over K = 20000 (2500 MMAs)
+// shrank results by ~1e-4 relative.  So the MMA accumulates only TC_CHUNK
+// K-blocks into a TMEM buffer; the epilogue warps add each chunk into FP32
+// registers (round-to-nearest) and write the sum once per segment.  Two TMEM
+// buffers (256 columns each) let the MMA fill one chunk while the epilogue
+// drains the other.
+//
+// Warp roles (12 warps, so that at most three share an SM sub-partition's
+// register file at 168 registers each): 0 = TMA producer, 1 = TMEM
+// allocation owner and MMA issuer (one thread), 2..9 = epilogue (warp w reads
+// TMEM lanes 32*(w%4)..+31; warps 2..5 take the first half of the columns,
+// 6..9 the second), 10..11 = converters.
 //
 // Stream-K: unit u = tile*KB + kb; block c owns units [U*c/G, U*(c+1)/G).  A
 // block's first and last segments may cover part of a tile's K range; those
@@ -45,7 +56,11 @@
 namespace ffq {
 
 constexpr int TC_BM = 128;
-constexpr int TC_THREADS = 384;
+constexpr int TC_CONV_WARPS = 2;
+constexpr int TC_THREADS = 32 * (2 + 8 + TC_CONV_WARPS);  // 12 warps: <= 3 per SM sub-partition
+constexpr int TC_CHUNK = 8;      // K-blocks per TMEM accumulation chunk (3-product kernels)
+constexpr int TC_MAX_NT = 224;   // widest N tile (columns) the epilogue registers hold
+constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_MAX_STAGES = 6;
 constexpr long long TC_SPIN = 4000000;
 
@@ -61,6 +76,8 @@ struct TcSched {
   float *C;
   float *part;      // [2G][128][ntile]
   int *ctl;
+  int vec4;         // C rows are 16-byte aligned (C % 16 == 0, ldc % 4 == 0)
+  int fix_rows;     // rows of a tile per fixup block (divides TC_BM)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -178,6 +195,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive 32-bit TMEM columns -> 8 registers per thread.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Segment iterator shared by all roles: block c walks units [u0, u1).
 struct SegIter {
   long long u, u1;
@@ -228,10 +257,13 @@ struct TcStage {
 };
 
 template <int BK, int NPROD, bool A_MN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __maxnreg__(168)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmBl, TcSched sc) {
   using S = TcStage<BK, NPROD, A_MN>;
+  // the single-product sketch keeps whole segments in TMEM: its accuracy is
+  // set by the TF32 operands, not by the accumulation
+  constexpr int CHUNK = (NPROD == 3) ? TC_CHUNK : (1 << 30);
   constexpr int A_BYTES = S::A_BYTES;
   constexpr int KSWZ = (BK == 32) ? 2 : 4;  // 128B / 64B swizzle of K-major rows
   constexpr int KROW = BK * 4;
@@ -260,18 +292,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&conv_bar[s], 4);
+      mbar_init(&conv_bar[s], TC_CONV_WARPS);
       mbar_init(&empty_bar[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
-      mbar_init(&acce_bar[b], 4);
+      mbar_init(&acce_bar[b], TC_EPI_WARPS);
     }
     mbar_init(&drain_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(&tmem_base))
                  : "memory");
@@ -331,50 +363,56 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int seg = 0;
+      int chunk = 0;
       int tile, kb0, kb1;
       SegIter my = it;
       const uint32_t IDESC = idesc_tf32(NT);
       bool ok = true;
       while (ok && my.next(tile, kb0, kb1)) {
-        const int b = seg & 1;
-        const uint32_t acc_ph = (uint32_t)((seg >> 1) & 1);
-        if (!mbar_wait(&acce_bar[b], acc_ph ^ 1u, abortp, sc.ctl)) break;
-        tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)(b * 256);
-        for (int kb = kb0; kb < kb1; ++kb) {
-          uint64_t *wb = S::CONVERT ? &conv_bar[s] : &full_bar[s];
-          if (!mbar_wait(wb, ph, abortp, sc.ctl)) {
+        for (int kc = kb0; kc < kb1 && ok; kc += CHUNK) {
+          const int kc1 = (kb1 - kc > CHUNK) ? kc + CHUNK : kb1;
+          const int b = chunk & 1;
+          const uint32_t acc_ph = (uint32_t)((chunk >> 1) & 1);
+          if (!mbar_wait(&acce_bar[b], acc_ph ^ 1u, abortp, sc.ctl)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t base = smem_u32(stage_ptr(s));
-          const uint32_t ah = base + S::AH, al = base + S::AL, bh = base + S::BH, bl = bh + B_BYTES;
+          const uint32_t dt = tmem + (uint32_t)(b * 256);
+          for (int kb = kc; kb < kc1; ++kb) {
+            uint64_t *wb = S::CONVERT ? &conv_bar[s] : &full_bar[s];
+            if (!mbar_wait(wb, ph, abortp, sc.ctl)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(stage_ptr(s));
+            const uint32_t ah = base + S::AH, al = base + S::AL, bh = base + S::BH, bl = bh + B_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < BK / 8; ++kk) {
-            // K-major operands: rows of BK*4 bytes in 8-row groups; K step of
-            // one MMA (8 TF32 values) = 32 bytes within the swizzled row.
-            const uint64_t da = smem_desc(ah + kk * 32, 16, 8 * KROW, KSWZ);
-            const uint64_t db = smem_desc(bh + kk * 32, 16, 8 * KROW, KSWZ);
-            const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-            mma_tf32(dt, da, db, IDESC, acc);
-            if (NPROD == 3) {
-              const uint64_t dal = smem_desc(al + kk * 32, 16, 8 * KROW, KSWZ);
-              const uint64_t dbl = smem_desc(bl + kk * 32, 16, 8 * KROW, KSWZ);
-              mma_tf32(dt, da, dbl, IDESC, 1u);
-              mma_tf32(dt, dal, db, IDESC, 1u);
+            for (int kk = 0; kk < BK / 8; ++kk) {
+              // K-major operands: rows of BK*4 bytes in 8-row groups; K step of
+              // one MMA (8 TF32 values) = 32 bytes within the swizzled row.
+              const uint64_t da = smem_desc(ah + kk * 32, 16, 8 * KROW, KSWZ);
+              const uint64_t db = smem_desc(bh + kk * 32, 16, 8 * KROW, KSWZ);
+              const uint32_t acc = (kb > kc || kk > 0) ? 1u : 0u;
+              mma_tf32(dt, da, db, IDESC, acc);
+              if (NPROD == 3) {
+                const uint64_t dal = smem_desc(al + kk * 32, 16, 8 * KROW, KSWZ);
+                const uint64_t dbl = smem_desc(bl + kk * 32, 16, 8 * KROW, KSWZ);
+                mma_tf32(dt, da, dbl, IDESC, 1u);
+                mma_tf32(dt, dal, db, IDESC, 1u);
+              }
+            }
+            mma_commit(&empty_bar[s]);
+            if (++s == STAGES) {
+              s = 0;
+              ph ^= 1u;
             }
           }
-          mma_commit(&empty_bar[s]);
-          if (++s == STAGES) {
-            s = 0;
-            ph ^= 1u;
-          }
+          if (!ok) break;
+          mma_commit(&accf_bar[b]);
+          ++chunk;
         }
-        if (!ok) break;
-        mma_commit(&accf_bar[b]);
-        ++seg;
       }
       if (*abortp) {
         // make sure no MMA is still writing TMEM before it is freed
@@ -383,17 +421,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     __syncwarp();
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 2 && warp < 2 + TC_EPI_WARPS) {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;
-    int seg = 0;
+    const int q = warp & 3;                        // TMEM lane quadrant
+    const int half = NT >> 1;                      // columns per warp (multiple of 8)
+    const int col0 = (warp >= 6) ? half : 0;       // this warp's first column
+    constexpr int NACC = TC_MAX_NT / 2;
+    int chunk = 0;
     int tile, kb0, kb1;
     SegIter my = it;
-    while (my.next(tile, kb0, kb1)) {
-      const int b = seg & 1;
-      const uint32_t acc_ph = (uint32_t)((seg >> 1) & 1);
-      if (!mbar_wait(&accf_bar[b], acc_ph, abortp, sc.ctl)) break;
-      tc_fence_after();
+    bool ok = true;
+    while (ok && my.next(tile, kb0, kb1)) {
+      float acc[NACC];
+#pragma unroll
+      for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
+      for (int kc = kb0; kc < kb1; kc += CHUNK) {
+        const int b = chunk & 1;
+        const uint32_t acc_ph = (uint32_t)((chunk >> 1) & 1);
+        if (!mbar_wait(&accf_bar[b], acc_ph, abortp, sc.ctl)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + col0);
+#pragma unroll
+        for (int g = 0; g < NACC / 8; ++g) {
+          if (g * 8 < half) {
+            float v[8];
+            tmem_ld8(ta + (uint32_t)(g * 8), v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[g * 8 + i] += v[i];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[b]);
+        ++chunk;
+      }
+      if (!ok) break;
       const int row_in_tile = q * 32 + lane;
       const int row = tile * TC_BM + row_in_tile;
       const bool full = (kb0 == 0 && kb1 == sc.KB);
@@ -407,30 +472,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         dst = sc.part + ((int64_t)(2 * c + slot) * TC_BM + row_in_tile) * sc.ntile;
         ncols = sc.ntile;
       }
-#pragma unroll 1
-      for (int c0 = 0; c0 < NT; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + c0), v);
-        if (dst) {
-          if (c0 + 32 <= ncols) {
-            float4 *d4 = reinterpret_cast<float4 *>(dst + c0);
+      if (dst) {
+        const bool v4 = !full || sc.vec4;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          } else {
+        for (int g = 0; g < NACC / 4; ++g) {
+          const int cc = col0 + 4 * g;
+          if (4 * g < half) {
+            if (v4 && cc + 4 <= ncols) {
+              *reinterpret_cast<float4 *>(dst + cc) =
+                  make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (c0 + i < ncols) dst[c0 + i] = v[i];
+              for (int i = 0; i < 4; ++i)
+                if (cc + i < ncols) dst[cc + i] = acc[4 * g + i];
+            }
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce_bar[b]);
-      ++seg;
     }
-  } else if (warp >= 8 && S::CONVERT) {
+  } else if (warp >= 2 + TC_EPI_WARPS && S::CONVERT) {
     // ---------------- converters ----------------
-    const int ct = threadIdx.x - 256;  // 0..127: tile row m (A_MN) or 16-byte chunk index
+    constexpr int NCT = 32 * TC_CONV_WARPS;
+    const int ct = threadIdx.x - 32 * (2 + TC_EPI_WARPS);  // 0..NCT-1
     int s = 0;
     uint32_t ph = 0;
     int tile, kb0, kb1;
@@ -444,8 +507,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         unsigned char *st = stage_ptr(s);
         if (A_MN) {
-          // transpose row m = ct of the m-contiguous tile into K-major rows
-          const int m = ct;
+          // transpose rows m = ct, ct + NCT, ... of the m-contiguous tile
+          // into K-major rows
+#pragma unroll 1
+          for (int m = ct; m < TC_BM; m += NCT)
 #pragma unroll
           for (int k4 = 0; k4 < BK; k4 += 4) {
             float x[4];
@@ -473,7 +538,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           float4 *a4 = reinterpret_cast<float4 *>(st + S::AH);
           float4 *l4 = reinterpret_cast<float4 *>(st + S::AL);
 #pragma unroll 4
-          for (int i = ct; i < A_BYTES / 16; i += 128) {
+          for (int i = ct; i < A_BYTES / 16; i += NCT) {
             const float4 x = a4[i];
             float4 h, l;
             h.x = tf32_head(x.x);
@@ -501,39 +566,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // teardown
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
 }
 
+constexpr int TC_MAX_GRID = 1024;  // upper bound of the persistent grid (fixup slot table)
+
 // Sum the partial pieces of the tiles that several blocks share, in block
-// order, and write them to C.  One block per (tile, 32-row slab).
+// order (deterministic), and write them to C.  Grid (tiles, TC_BM /
+// sc.fix_rows): one block per sc.fix_rows rows of a tile.
 __global__ void tc_fixup_kernel(TcSched sc) {
+  __shared__ int s_lo, s_hi;
+  __shared__ unsigned char s_slot[TC_MAX_GRID];
   const int tile = blockIdx.x;
-  const long long ua = (long long)tile * sc.KB, ub = ua + sc.KB - 1;
-  auto owner = [&](long long u) {
-    long long lo = 0, hi = sc.G - 1;
-    while (lo < hi) {
-      const long long mid = (lo + hi + 1) / 2;
-      if ((sc.U * mid) / sc.G <= u) lo = mid;
-      else hi = mid - 1;
-    }
-    return (int)lo;
-  };
-  const int c_lo = owner(ua), c_hi = owner(ub);
+  if (threadIdx.x == 0) {
+    const long long ua = (long long)tile * sc.KB, ub = ua + sc.KB - 1;
+    auto owner = [&](long long u) {
+      long long lo = 0, hi = sc.G - 1;
+      while (lo < hi) {
+        const long long mid = (lo + hi + 1) / 2;
+        if ((sc.U * mid) / sc.G <= u) lo = mid;
+        else hi = mid - 1;
+      }
+      return (int)lo;
+    };
+    s_lo = owner(ua);
+    s_hi = owner(ub);
+  }
+  __syncthreads();
+  const int c_lo = s_lo, c_hi = s_hi;
   if (c_lo == c_hi) return;  // written directly by its only owner
-  const int r0 = blockIdx.y * 32;
-  for (int e = threadIdx.x; e < 32 * sc.N; e += blockDim.x) {
+  // slot of this tile in each contributor's partial buffer: 0 if it is the
+  // contributor's first tile, else 1
+  for (int cb = c_lo + threadIdx.x; cb <= c_hi; cb += blockDim.x)
+    s_slot[cb - c_lo] = (tile == (int)(((sc.U * cb) / sc.G) / sc.KB)) ? 0 : 1;
+  __syncthreads();
+  const int r0 = blockIdx.y * sc.fix_rows;
+  for (int e = threadIdx.x; e < sc.fix_rows * sc.N; e += blockDim.x) {
     const int rr = r0 + e / sc.N, col = e % sc.N;
     const int row = tile * TC_BM + rr;
     if (row >= sc.M) continue;
     float acc = 0.f;
-    for (int cb = c_lo; cb <= c_hi; ++cb) {
-      const int ft = (int)(((sc.U * cb) / sc.G) / sc.KB);
-      const int slot = (tile == ft) ? 0 : 1;
-      acc += sc.part[((int64_t)(2 * cb + slot) * TC_BM + rr) * sc.ntile + col];
-    }
+    for (int cb = c_lo; cb <= c_hi; ++cb)
+      acc += sc.part[((int64_t)(2 * cb + s_slot[cb - c_lo]) * TC_BM + rr) * sc.ntile + col];
     sc.C[(int64_t)row * sc.ldc + col] = acc;
   }
 }
@@ -550,6 +627,29 @@ __global__ void split_tf32_kernel(const float *__restrict__ B, int64_t ld, int64
     const float h = tf32_head(x);
     Bh[i * ld + j] = h;
     Bl[i * ld + j] = x - h;
+  }
+}
+
+// Dh / Dl (cols x rows, leading dimension ldd) = TF32 head / tail of Src^T,
+// Src rows x cols with leading dimension lds: the K-major thin operand of a
+// tensor-core product.  32 x 32 tiles through shared memory, block (32, 8).
+__global__ void transpose_split_kernel(const float *__restrict__ Src, int64_t lds, int64_t rows, int64_t cols,
+                                       float *__restrict__ Dh, float *__restrict__ Dl, int64_t ldd) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t r = r0 + yy, c = c0 + threadIdx.x;
+    tile[yy][threadIdx.x] = (r < rows && c < cols) ? Src[r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t dr = c0 + yy, dc = r0 + threadIdx.x;  // Dst row = Src column
+    if (dr < cols && dc < rows) {
+      const float x = tile[threadIdx.x][yy];
+      const float h = tf32_head(x);
+      Dh[dr * ldd + dc] = h;
+      Dl[dr * ldd + dc] = x - h;
+    }
   }
 }
 
