@@ -35,10 +35,13 @@ __global__ void gather_rows_kernel(const T *__restrict__ Src, int64_t lds, int k
 }
 
 // R11 (k x k) = upper triangle of G(:, J) where G^T = Gt (n x ldg):
-// R11(i, j) = Gt[piv[j], i] for i <= j.
+// R11(i, j) = Gt[piv[j], i] for i <= j.  Skipped when gate is given and
+// *gate == 0 (the device-side swap count: nothing to redo without swaps).
 template <typename T>
 __global__ void extract_r11_kernel(const T *__restrict__ Gt, int64_t ldg, int k,
-                                   const int32_t *__restrict__ piv, T *__restrict__ R11) {
+                                   const int32_t *__restrict__ piv, T *__restrict__ R11,
+                                   const int *gate) {
+  if (gate && *gate == 0) return;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
     const int i = e / k, j = e - i * k;
     R11[e] = (i <= j) ? Gt[(int64_t)piv[j] * ldg + i] : T(0);
@@ -85,7 +88,8 @@ __global__ void transpose_kernel(const T *__restrict__ Src, int64_t lds, int64_t
 template <typename T, int NS, int R, bool FWD>
 __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64_t ldx, int64_t M,
                                                         int k, const T *__restrict__ Pm,
-                                                        int64_t psi, int64_t psj) {
+                                                        int64_t psi, int64_t psj, const int *gate) {
+  if (gate && *gate == 0) return;  // gated recomputation (see extract_r11_kernel)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ps = reinterpret_cast<T *>(smem_raw);  // k x k, row-major, P(j, c) at Ps[j*k + c]
   T *dinv = Ps + (size_t)k * k;             // 1 / P(j, j)
@@ -655,7 +659,8 @@ __global__ void scale_cols_kernel(T *__restrict__ X, int64_t ldx, int64_t rows, 
 // Copy a rows x cols block between leading dimensions.
 template <typename T>
 __global__ void copy2d_kernel(const T *__restrict__ Src, int64_t lds, T *__restrict__ Dst, int64_t ldd,
-                              int64_t rows, int64_t cols) {
+                              int64_t rows, int64_t cols, const int *gate) {
+  if (gate && *gate == 0) return;
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {

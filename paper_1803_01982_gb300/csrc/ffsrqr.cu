@@ -9,7 +9,7 @@
 //   a5  G^T = A^T Q1  (= (R11 R12)^T, original column order)    pass 2 over A
 //   a6  R11 = triu(G(:, J)); Z^T = G^T R11^{-T}; trailing-norm estimate
 //       r_i = ||B(:,i) - B_J Z(:,i)||^2 / s; candidate c; alpha; g2  (Alg. 4)
-//   a7  swap loop while g2 > g (Alg. 4)                         [ffsrqr_swap.cuh]
+//   a7  swap loop while g2 > g (Alg. 4)                         [srqr_swap.cuh]
 //   a8  V' = orth(Z^T) = Pi Qhat1 up to a k x k rotation         (Alg. 9, line 2)
 //   a9  tmp = A V'                                               pass 3 over A
 //   a10 Y_t = tmp (R11 R_z^T)^{-1}; CholeskyQR2(Y_t) -> Q_t, R_t;
@@ -35,6 +35,7 @@
 #include "jacobi.cuh"
 #include "philox.cuh"
 #include "qrcp.cuh"
+#include "srqr_swap.cuh"
 #include "tc_gemm.cuh"
 
 #include <cudaTypedefs.h>
@@ -92,6 +93,9 @@ struct ffsrqr_plan_s {
   size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
   size_t off_sinv, off_sh, off_sl, off_scr;   // tensor-core small products (FFSRQR_MIXED)
   size_t off_jlog;                            // Jacobi rotation log
+  size_t off_rowk, off_qk, off_rot, off_rd, off_xinv, off_swpart, off_swbv, off_swbi;  // swap loop
+  int swap_grid;
+  size_t swap_smem;
   size_t part_cap;  // elements of the split-K buffer
   int qrcp_grid, qrcp_threads;
   int smem_optin;  // max dynamic shared memory per block (bytes)
@@ -283,7 +287,7 @@ bool tc_ok(const void *A, int64_t lda) {
 
 template <typename T, bool FWD>
 int launch_trsm(cudaStream_t st, const ffsrqr_plan_s *P, T *X, int64_t ldx, int64_t M, const T *Pm,
-                int64_t psi, int64_t psj) {
+                int64_t psi, int64_t psj, const int *gate = nullptr) {
   const int k = P->k;
   const size_t smem = (size_t)k * (k + 1) * sizeof(T);
   const int threads = 512;
@@ -299,7 +303,7 @@ int launch_trsm(cudaStream_t st, const ffsrqr_plan_s *P, T *X, int64_t ldx, int6
     auto fn = few ? trsm_rows_kernel<T, NSv, 1, FWD>                                          \
                   : trsm_rows_kernel<T, NSv, (sizeof(T) == 4) ? 8 : 4, FWD>;                  \
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-    fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj);                              \
+    fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj, gate);                        \
     CKL("trsm_rows");                                                                         \
     return 0;                                                                                 \
   }
@@ -613,6 +617,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
                             (int)P->qrcp_smem));
     CK(cudaLaunchCooperativeKernel((void *)qrcp_kernel<T>, dim3(P->qrcp_grid), dim3(P->qrcp_threads),
                                    args, P->qrcp_smem, st));
+    ++g_launches;
   }
   posdiag_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.s11, k);
   CKL("posdiag");
@@ -637,13 +642,13 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   }
   MARK(5);
   // a6: R11, R11^{-1}, Z^T = G^T R11^{-T}
-  extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11);
+  extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11, nullptr);
   CKL("extract_r11");
   eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k, k);
   CKL("eye");
   if ((rc = launch_trsm<T, true>(st, P, w.rinv, k, k, w.r11, k, 1))) return rc;
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, w.zt,
-                                                                                          ldk, n, k);
+                                                                                          ldk, n, k, nullptr);
   CKL("copy_zt");
   if ((rc = launch_trsm<T, false>(st, P, w.zt, ldk, n, w.r11, 1, k))) return rc;
   // trailing-norm estimate and the first SRQR test
@@ -663,14 +668,58 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
     if ((rc = srqr_test<T>(st, P, w, A, lda, 1))) return rc;
   }
   MARK(6);
-  // a7: swap loop (Alg. 4) runs here when g2 > g
+  // a7: swap loop (Alg. 4) while g2 > g, entirely on the device; afterwards
+  // R11 and Z^T are rebuilt for the final column set (skipped on the device
+  // when no swap happened)
+  if (k < n) {
+    SwapArgs<T> sa;
+    sa.A = A;
+    sa.lda = lda;
+    sa.m = m;
+    sa.n = n;
+    sa.k = k;
+    sa.gt = w.gt;
+    sa.ldg = ldk;
+    sa.rowk = reinterpret_cast<T *>(ws + P->off_rowk);
+    sa.q1 = w.q1;
+    sa.ldq = ldk;
+    sa.qk = reinterpret_cast<T *>(ws + P->off_qk);
+    sa.z = w.z;
+    sa.r = w.r;
+    sa.sel = w.sel;
+    sa.piv = piv;
+    sa.rot = reinterpret_cast<T *>(ws + P->off_rot);
+    sa.Rd = reinterpret_cast<T *>(ws + P->off_rd);
+    sa.X = reinterpret_cast<T *>(ws + P->off_xinv);
+    sa.part = reinterpret_cast<T *>(ws + P->off_swpart);
+    sa.bv = reinterpret_cast<T *>(ws + P->off_swbv);
+    sa.bi = reinterpret_cast<int *>(ws + P->off_swbi);
+    sa.ctl = w.ctl;
+    sa.dctl = w.dctl;
+    sa.g = P->g;
+    sa.max_swaps = P->max_swaps;
+    sa.spin_limit = kSpinLimit;
+    void *args[] = {&sa};
+    CK(cudaFuncSetAttribute(srqr_swap_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)P->swap_smem));
+    CK(cudaLaunchCooperativeKernel((void *)srqr_swap_kernel<T>, dim3(P->swap_grid), dim3(512), args,
+                                   P->swap_smem, st));
+    ++g_launches;
+    const int *gate = w.ctl + CTL_SWAPS;
+    extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11, gate);
+    CKL("extract_r11_swapped");
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, w.zt,
+                                                                                            ldk, n, k, gate);
+    CKL("copy_zt_swapped");
+    if ((rc = launch_trsm<T, false>(st, P, w.zt, ldk, n, w.r11, 1, k, gate))) return rc;
+  }
   MARK(7);
   // a8: V' = orth(Z^T), R_z
   if (tc) {
     if ((rc = cholqr2_tc(st, P, ws, (const float *)w.zt, n, (float *)w.vp, (float *)w.rz))) return rc;
   } else {
     copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.zt, ldk, w.vp,
-                                                                                            ldk, n, k);
+                                                                                            ldk, n, k, nullptr);
     CKL("copy_vp");
     if ((rc = cholqr2<T>(st, P, ws, w.vp, ldk, n, w.rz))) return rc;
   }
@@ -685,7 +734,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   MARK(9);
   // a10: Y_t = tmp R_z^{-T} R11^{-1}; CholeskyQR2 -> Q_t, R_t; M_t = R_t R11 R_z^T
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(w.tmp, ldk, w.yt,
-                                                                                          ldk, m, k);
+                                                                                          ldk, m, k, nullptr);
   CKL("copy_yt");
   if ((rc = launch_trsm<T, false>(st, P, w.yt, ldk, m, w.rz, 1, k))) return rc;
   if ((rc = launch_trsm<T, true>(st, P, w.yt, ldk, m, w.r11, k, 1))) return rc;
@@ -794,6 +843,14 @@ void layout(ffsrqr_plan_s *P) {
     const int kk = k + (k & 1);
     P->off_jlog = take((size_t)JAC_MAX_SWEEPS * (kk - 1) * (kk / 2) * 2 * E);  // Jacobi rotation log
   }
+  P->off_rowk = take((size_t)n * E);
+  P->off_qk = take((size_t)m * E);
+  P->off_rot = take((size_t)2 * k * E);
+  P->off_rd = take((size_t)k * k * E);
+  P->off_xinv = take((size_t)k * k * E);
+  P->off_swpart = take((size_t)P->swap_grid * std::max<int64_t>(n, k + 1) * E);
+  P->off_swbv = take((size_t)P->swap_grid * E);
+  P->off_swbi = take((size_t)P->swap_grid * sizeof(int));
   P->nblk_sign = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(std::max(m, n), 64), nsm));
   P->off_sgnv = take((size_t)P->nblk_sign * k * E);
   P->off_sgni = take((size_t)P->nblk_sign * k * sizeof(int));
@@ -860,6 +917,12 @@ int plan_qrcp(ffsrqr_plan_s *P) {
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel<T>, P->qrcp_threads, P->qrcp_smem));
   if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
   P->qrcp_grid = (int)grid;
+  // swap loop: one co-resident block of 512 threads per SM
+  P->swap_smem = (size_t)(P->k + 1 + 2 * P->k + 16 * P->k) * sizeof(T);
+  CK(cudaFuncSetAttribute(srqr_swap_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->swap_smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srqr_swap_kernel<T>, 512, P->swap_smem));
+  if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
+  P->swap_grid = P->num_sms;
   return 0;
 }
 

