@@ -49,12 +49,16 @@ __global__ void extract_r11_kernel(const T *__restrict__ Gt, int64_t ldg, int k,
 }
 
 // Make the diagonal of an upper-triangular k x k matrix non-negative by
-// flipping rows (left multiplication by a sign matrix).
+// flipping rows (left multiplication by a sign matrix).  One warp per row:
+// every lane reads the diagonal before any lane writes the row.
 template <typename T>
 __global__ void posdiag_rows_kernel(T *__restrict__ R, int k) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
-    const int i = e / k;
-    if (R[(int64_t)i * k + i] < T(0)) R[e] = -R[e];
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < k; i += (gridDim.x * blockDim.x) >> 5) {
+    const bool neg = R[(int64_t)i * k + i] < T(0);
+    __syncwarp();
+    if (neg)
+      for (int j = lane; j < k; j += 32) R[(int64_t)i * k + j] = -R[(int64_t)i * k + j];
   }
 }
 

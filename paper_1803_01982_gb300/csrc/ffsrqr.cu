@@ -619,7 +619,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
                                    args, P->qrcp_smem, st));
     ++g_launches;
   }
-  posdiag_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.s11, k);
+  posdiag_rows_kernel<T><<<(unsigned)cdiv((int64_t)k * 32, 256), 256, 0, st>>>(w.s11, k);
   CKL("posdiag");
   MARK(3);
   // a4: panel Y = A_J S11^{-1}, CholeskyQR2 -> Q1
