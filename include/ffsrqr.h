@@ -146,6 +146,15 @@ int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int6
  * written, -1 for a NULL plan, -2 if the plan was made without the flag. */
 int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap);
 
+/* The same for the last run (back = 0) or the run before it (back = 1): a
+ * plan keeps two sets of events and alternate runs record into alternate
+ * sets, so the times of run i can be read while run i + 1 is already
+ * enqueued.  Waits on the host until that run's last event has completed.
+ * Returns the count written, -1 NULL plan,
+ * -2 plan without FFSRQR_FLAG_PHASE_TIMES, -3 back outside [0, 1] or no
+ * such run yet, -4 NULL ms, FFSRQR_STATUS_CUDA if the wait fails. */
+int ffsrqr_phase_times_back(ffsrqr_plan_t plan, int32_t back, float *ms, int32_t cap);
+
 /* Number of kernels the last ffsrqr_run of this plan enqueued (-1 for NULL). */
 int ffsrqr_launch_count(ffsrqr_plan_t plan);
 

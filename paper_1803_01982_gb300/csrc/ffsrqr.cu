@@ -105,15 +105,19 @@ struct ffsrqr_plan_s {
   int nblk_res; // blocks of the SRQR residual kernels
   int nblk_sign;
   Item items[9];
-  cudaEvent_t ev[13];  // phase events (FFSRQR_FLAG_PHASE_TIMES)
-  cudaEvent_t ev_tc[3][2];  // around each tensor-core pass kernel
+  // phase events (FFSRQR_FLAG_PHASE_TIMES), two sets used by alternate runs
+  // so that a run's times can be read while the next run executes
+  cudaEvent_t ev[2][13];
+  cudaEvent_t ev_tc[2][3][2];  // around each tensor-core pass kernel
+  int evset;                   // set of the current / last run
+  long long runs;
   int launches;        // kernel launches of the last run
   bool ev_ok;
 };
 
 #define MARK(i)                                                          \
   do {                                                                   \
-    if (P->ev_ok) cuda_ok(cudaEventRecord(P->ev[(i)], st), "event");     \
+    if (P->ev_ok) cuda_ok(cudaEventRecord(P->ev[P->evset][(i)], st), "event"); \
   } while (0)
 
 namespace {
@@ -264,9 +268,9 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   {                                                                                                  \
     auto fn = tc_gemm_kernel<BKv, NPv, AMNv>;                                                        \
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));            \
-    if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[pass][0], st);                               \
+    if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[P->evset][pass][0], st);                     \
     fn<<<sc.G, TC_THREADS, smem, st>>>(mA, mB, mBl, sc);                                             \
-    if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[pass][1], st);                               \
+    if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[P->evset][pass][1], st);                     \
   }
   if (nprod == 1 && a_mn) TC_LAUNCH(32, 1, true)
   else if (nprod == 3 && a_mn) TC_LAUNCH(16, 3, true)
@@ -974,8 +978,11 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
   P->ev_ok = false;
   if (P->flags & FFSRQR_FLAG_PHASE_TIMES) {
     bool ok = true;
-    for (int i = 0; i < 13 && ok; ++i) ok = cuda_ok(cudaEventCreate(&P->ev[i]), "cudaEventCreate");
-    for (int i = 0; i < 6 && ok; ++i) ok = cuda_ok(cudaEventCreate(&P->ev_tc[i / 2][i % 2]), "cudaEventCreate");
+    for (int e = 0; e < 2; ++e) {
+      for (int i = 0; i < 13 && ok; ++i) ok = cuda_ok(cudaEventCreate(&P->ev[e][i]), "cudaEventCreate");
+      for (int i = 0; i < 6 && ok; ++i)
+        ok = cuda_ok(cudaEventCreate(&P->ev_tc[e][i / 2][i % 2]), "cudaEventCreate");
+    }
     if (!ok) {
       delete P;
       return FFSRQR_STATUS_CUDA;
@@ -1005,6 +1012,8 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
   g_launches = 0;
+  plan->evset = (int)(plan->runs & 1);
+  ++plan->runs;
   int rc;
   if (plan->elem == 8)
     rc = run_impl<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S, (double *)V,
@@ -1019,8 +1028,10 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
 int ffsrqr_destroy(ffsrqr_plan_t plan) {
   if (!plan) return -1;
   if (plan->ev_ok) {
-    for (int i = 0; i < 13; ++i) cudaEventDestroy(plan->ev[i]);
-    for (int i = 0; i < 6; ++i) cudaEventDestroy(plan->ev_tc[i / 2][i % 2]);
+    for (int e = 0; e < 2; ++e) {
+      for (int i = 0; i < 13; ++i) cudaEventDestroy(plan->ev[e][i]);
+      for (int i = 0; i < 6; ++i) cudaEventDestroy(plan->ev_tc[e][i / 2][i % 2]);
+    }
   }
   delete plan;
   return 0;
@@ -1044,23 +1055,35 @@ const char *ffsrqr_status_string(int code) {
 
 const char *ffsrqr_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
-int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap) {
+int ffsrqr_phase_times_back(ffsrqr_plan_t plan, int32_t back, float *ms, int32_t cap) {
   if (!plan) return -1;
   if (!plan->ev_ok) return -2;
+  if (back < 0 || back > 1 || plan->runs <= back) return -3;
+  if (!ms && cap > 0) return -4;
+  const int e = (int)((plan->runs - 1 - back) & 1);
+  // host wait for that run's last event (the next run may still execute)
+  if (cudaEventSynchronize(plan->ev[e][12]) != cudaSuccess) return FFSRQR_STATUS_CUDA;
   int cnt = 0;
   for (int i = 0; i < 12 && cnt < cap; ++i, ++cnt) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, plan->ev[i], plan->ev[i + 1]) != cudaSuccess) t = -1.f;
+    if (cudaEventElapsedTime(&t, plan->ev[e][i], plan->ev[e][i + 1]) != cudaSuccess) t = -1.f;
     ms[cnt] = t;
   }
   for (int i = 0; i < 3 && cnt < cap; ++i, ++cnt) {
     float t = -1.f;
     if (plan->mode == FFSRQR_MIXED &&
-        cudaEventElapsedTime(&t, plan->ev_tc[i][0], plan->ev_tc[i][1]) != cudaSuccess)
+        cudaEventElapsedTime(&t, plan->ev_tc[e][i][0], plan->ev_tc[e][i][1]) != cudaSuccess)
       t = -1.f;
     ms[cnt] = t;
   }
   return cnt;
+}
+
+int ffsrqr_phase_times(ffsrqr_plan_t plan, float *ms, int32_t cap) {
+  if (!plan) return -1;
+  if (!plan->ev_ok) return -2;
+  if (plan->runs < 1) return -3;
+  return ffsrqr_phase_times_back(plan, 0, ms, cap);
 }
 
 int ffsrqr_launch_count(ffsrqr_plan_t plan) {

@@ -66,6 +66,8 @@ def _load():
     lib.ffsrqr_philox4x32_10.restype = ctypes.c_int
     lib.ffsrqr_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
     lib.ffsrqr_phase_times.restype = ctypes.c_int
+    lib.ffsrqr_phase_times_back.argtypes = [P, i32, ctypes.POINTER(ctypes.c_float), i32]
+    lib.ffsrqr_phase_times_back.restype = ctypes.c_int
     lib.ffsrqr_launch_count.argtypes = [P]
     lib.ffsrqr_launch_count.restype = ctypes.c_int
     return lib
@@ -83,6 +85,7 @@ ffsrqr_workspace_item = lib.ffsrqr_workspace_item
 ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
 ffsrqr_phase_times = lib.ffsrqr_phase_times
 ffsrqr_launch_count = lib.ffsrqr_launch_count
+ffsrqr_phase_times_back = lib.ffsrqr_phase_times_back
 
 
 class FfsrqrError(RuntimeError):
@@ -178,10 +181,12 @@ FLAG_CHECK_FINITE = 1
 FLAG_PHASE_TIMES = 2
 
 
-def phase_times(plan: "Plan") -> dict:
-    """Per-phase device milliseconds of the plan's last run (FLAG_PHASE_TIMES)."""
+def phase_times(plan: "Plan", back: int = 0) -> dict:
+    """Per-phase device milliseconds of the plan's last run (back = 0) or the
+    run before it (back = 1), for a plan made with FLAG_PHASE_TIMES; waits on
+    the host for that run to finish."""
     buf = (ctypes.c_float * 15)()
-    cnt = lib.ffsrqr_phase_times(plan._h, buf, 15)
+    cnt = lib.ffsrqr_phase_times_back(plan._h, back, buf, 15)
     if cnt < 0:
-        raise FfsrqrError("plan was created without FLAG_PHASE_TIMES")
+        raise FfsrqrError(f"ffsrqr_phase_times_back returned {cnt}")
     return {PHASES[i]: buf[i] for i in range(cnt)}
