@@ -17,9 +17,10 @@ Functions (row-major float64 arrays):
 * ``ffsrqr(A, k, p, seed, ...)``  -- Alg. 9, returns U, S, V, piv, info, trace
 * ``residual_fro(A, U, S, V)``    -- ||A - U diag(S) V^T||_F
 
-Parity caveats (no pin possible): the pivot sequence inside the SRQR swap loop
-is fixed only by the invariants the tests check (factorisation identity,
-termination with g2 <= g, Rayleigh-Ritz closed form of the final result).
+The SRQR swap loop has no printed worked example; it is pinned through the
+invariants the mathematics fixes (factorisation identity and orthonormal Q
+after the swaps, |det R11| growing by more than g per swap, termination with
+g2 <= g or the cap status).
 """
 from __future__ import annotations
 
