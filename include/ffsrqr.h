@@ -166,6 +166,35 @@ int ffsrqr_launch_count(ffsrqr_plan_t plan);
  * count < 0, FFSRQR_STATUS_CUDA on launch failure. */
 int ffsrqr_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int32_t count, void *stream);
 
+/* Partial QR with column pivoting of a sketch B (s x n), k steps: Alg. 1
+ * applied to B as in Alg. 2 -- the step ffsrqr_run performs after pass 1 --
+ * for callers that cannot allocate device memory at the point of the call.
+ * The entry point itself has no counterpart in the paper: it only places the
+ * step's scratch (candidate columns, control words, selection flags) in a
+ * fixed device array of this library instead of a caller workspace.
+ *   Bt     device, n x lds row-major FP32: B^T (column i of B is row i).
+ *   piv    device, k int32 out: the pivots (original column indices, in
+ *          pivot order; greedy largest trailing norm, ties to the lowest
+ *          index).
+ *   S11    device, k x k row-major FP32 out: the R factor of the pivoted
+ *          columns, rows flipped so that its diagonal is non-negative.
+ *   status device int32 out or NULL: 0, FFSRQR_STATUS_RANK_DEFICIENT (a zero
+ *          trailing norm) or FFSRQR_STATUS_TIMEOUT (bounded wait expired).
+ * Limits of the static scratch: n <= 65536, lds <= 256 (so s <= 256), and
+ * the sketch must fit the blocks' shared memory (else
+ * FFSRQR_STATUS_UNSUPPORTED).  Nothing is allocated: the scratch is resolved
+ * once per device on the first call (host-side set-up; make that call first,
+ * outside any stream capture) and the words that must start at zero are
+ * cleared with cudaMemsetAsync on stream.  Calls on one device share the
+ * scratch, so calls that may execute at the same time race: order them on
+ * one stream or with events.  Enqueues only; results valid after the stream
+ * is synchronised.  Returns 0, -i for an invalid i-th argument (1 Bt, 2 n,
+ * 3 s, 4 lds < s, 5 k outside [1, min(s, n)], 6 piv, 7 S11),
+ * FFSRQR_STATUS_UNSUPPORTED beyond the limits, FFSRQR_STATUS_CUDA on a CUDA
+ * error. */
+int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t lds, int32_t k, int32_t *piv,
+                       float *S11, int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,8 @@ def _load():
     lib.ffsrqr_phase_times_back.restype = ctypes.c_int
     lib.ffsrqr_launch_count.argtypes = [P]
     lib.ffsrqr_launch_count.restype = ctypes.c_int
+    lib.ffsrqr_qrcp_static.argtypes = [P, i64, i32, i64, i32, P, P, P, P]
+    lib.ffsrqr_qrcp_static.restype = ctypes.c_int
     return lib
 
 
@@ -86,6 +88,7 @@ ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
 ffsrqr_phase_times = lib.ffsrqr_phase_times
 ffsrqr_launch_count = lib.ffsrqr_launch_count
 ffsrqr_phase_times_back = lib.ffsrqr_phase_times_back
+ffsrqr_qrcp_static = lib.ffsrqr_qrcp_static
 
 
 class FfsrqrError(RuntimeError):
