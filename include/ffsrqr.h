@@ -195,6 +195,126 @@ int ffsrqr_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int32_t count, 
 int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t lds, int32_t k, int32_t *piv,
                        float *S11, int32_t *status, void *stream);
 
+
+/* ------------------------------------------------------------------------ */
+/* Batched problems (many uneven rank-k approximations as one graph launch) */
+/* ------------------------------------------------------------------------ */
+/* Not a step of the paper's algorithm: a way to run Alg. 9 on many matrices
+ * at once (e.g. the mode unfoldings of a Tucker decomposition or the iterates
+ * of singular-value thresholding, the paper's applications). */
+typedef struct ffsrqr_batch_s *ffsrqr_batch_t;
+
+/* One problem's device buffers, as in ffsrqr_run. */
+typedef struct {
+  const void *A;
+  int64_t lda;
+  uint64_t seed;
+  void *U;
+  int64_t ldu;
+  void *S;
+  void *V;
+  int64_t ldv;
+  int32_t *piv;
+} ffsrqr_problem_t;
+
+/* Plans count problems (sizes m[i] x n[i], rank k[i], oversampling p[i], one
+ * mode and opts for all) and lays their workspaces out in one buffer of
+ * *workspace_bytes (256-byte aligned slices).  streams (1..64): concurrent
+ * streams the batch graph uses.  Returns 0, -1 NULL batch, -2 count < 1,
+ * -3 NULL size arrays, -8 streams outside [1, 64], -9 NULL workspace_bytes,
+ * or the ffsrqr_plan code of the first problem that fails to plan. */
+int ffsrqr_batch_create(ffsrqr_batch_t *batch, int32_t count, const int64_t *m, const int64_t *n,
+                        const int32_t *k, const int32_t *p, int32_t mode, const ffsrqr_opts_t *opts,
+                        int32_t streams, size_t *workspace_bytes);
+
+/* Runs every problem (probs[count], infos[count] pinned host or NULL).  On
+ * the first call, or when probs / workspace / infos / the stream count
+ * differ from the previous call, the pipelines of all problems are captured
+ * into one CUDA graph (stream forked into the batch's streams, problems in
+ * decreasing m*n round-robin over them, joined back); the graph is then
+ * launched on stream.  Later calls with the same arguments only launch it.
+ * Returns 0, -1 NULL batch, -2 NULL probs, -3 NULL or unaligned workspace,
+ * the ffsrqr_run code of a problem, or FFSRQR_STATUS_CUDA. */
+int ffsrqr_batch_run(ffsrqr_batch_t batch, const ffsrqr_problem_t *probs, void *workspace, void *stream,
+                     ffsrqr_info_t *infos);
+
+/* Autotuner: times the batch graph (3 launches after a warm-up) with 1, 2,
+ * 4 and 8 streams on stream and keeps the fastest; writes it to *chosen and
+ * its milliseconds per launch to *ms_best (either may be NULL).  The batch's
+ * outputs hold the results of the last timed launch.  Returns as
+ * ffsrqr_batch_run. */
+int ffsrqr_batch_tune(ffsrqr_batch_t batch, const ffsrqr_problem_t *probs, void *workspace, void *stream,
+                      ffsrqr_info_t *infos, int32_t *chosen, float *ms_best);
+
+/* Current stream count of the batch (-1 for NULL). */
+int ffsrqr_batch_streams(ffsrqr_batch_t batch);
+
+/* Byte offset of problem i's workspace slice and its plan (for
+ * ffsrqr_workspace_item).  Returns 0, -1 NULL batch, -2 i out of range. */
+int ffsrqr_batch_workspace_offset(ffsrqr_batch_t batch, int32_t i, size_t *offset, ffsrqr_plan_t *plan);
+
+int ffsrqr_batch_destroy(ffsrqr_batch_t batch);
+
+/* ------------------------------------------------------------------------ */
+/* Request server (admission under a memory budget, continuous batching)    */
+/* ------------------------------------------------------------------------ */
+/* Not a step of the paper's algorithm: a serving loop for streams of
+ * truncated-SVD requests such as the singular-value-thresholding iterates of
+ * the paper's robust PCA and matrix completion applications. */
+typedef struct ffsrqr_server_s *ffsrqr_server_t;
+
+/* One request: sizes and mode as in ffsrqr_plan, buffers as in ffsrqr_run
+ * (device memory owned by the caller until the request is finished). */
+typedef struct {
+  int64_t m, n;
+  int32_t k, p;
+  int32_t mode;
+  int32_t reserved;
+  const void *A;
+  int64_t lda;
+  uint64_t seed;
+  void *U;
+  int64_t ldu;
+  void *S;
+  void *V;
+  int64_t ldv;
+  int32_t *piv;
+} ffsrqr_request_t;
+
+/* Creates a server on the current device: one device arena of budget_bytes
+ * (the only device memory it allocates; request workspaces are carved from
+ * it first-fit), slots concurrent streams (1..64), options for every plan
+ * (NULL for the defaults), and a scheduler thread.  The scheduler admits
+ * queued requests in arrival order whenever a slot is free and the arena has
+ * room, and retires finished ones, so requests that arrive while others run
+ * start as resources free up and overlap on the device.  Returns 0, -1 NULL
+ * server, -2 budget below 4096, -3 slots outside [1, 64],
+ * FFSRQR_STATUS_WORKSPACE if the arena cannot be allocated, FFSRQR_STATUS_CUDA. */
+int ffsrqr_server_create(ffsrqr_server_t *server, size_t budget_bytes, int32_t slots, const ffsrqr_opts_t *opts);
+
+/* Queues a request; writes its ticket.  Returns 0, -1 NULL server, -2 NULL
+ * request or buffer, -3 NULL ticket, the ffsrqr_plan code for invalid sizes,
+ * or FFSRQR_STATUS_WORKSPACE when its workspace exceeds the whole budget
+ * (admission refused). */
+int ffsrqr_server_submit(ffsrqr_server_t server, const ffsrqr_request_t *req, int64_t *ticket);
+
+/* Non-blocking status of a ticket: 1 while queued or running; once finished
+ * writes its report and latency (seconds from submission to completion) and
+ * returns 0 (or the request's error code) -- a finished ticket is reported
+ * once, after which it is unknown (-2). */
+int ffsrqr_server_poll(ffsrqr_server_t server, int64_t ticket, ffsrqr_info_t *info, double *latency_s);
+
+/* Blocks until the ticket is finished; then as ffsrqr_server_poll. */
+int ffsrqr_server_wait(ffsrqr_server_t server, int64_t ticket, ffsrqr_info_t *info, double *latency_s);
+
+/* Counters: requests admitted, finished, still queued, and free arena bytes
+ * (any pointer may be NULL). */
+int ffsrqr_server_stats(ffsrqr_server_t server, int64_t *admitted, int64_t *completed, int64_t *queued,
+                        size_t *arena_free);
+
+/* Stops the scheduler (running requests finish first) and frees the arena. */
+int ffsrqr_server_destroy(ffsrqr_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,9 @@ struct Item {
 
 }  // namespace
 
+// Shared with the batch and server translation units (not part of the C ABI).
+void ffq_set_last_error(const char *what, cudaError_t e) { cuda_ok(e, what); }
+
 struct ffsrqr_plan_s {
   int64_t m, n;
   int k, p, s, mode;

@@ -40,6 +40,22 @@ class Info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Problem(ctypes.Structure):
+    """ffsrqr_problem_t: one problem of a batch (device pointers)."""
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64), ("S", ctypes.c_void_p),
+                ("V", ctypes.c_void_p), ("ldv", ctypes.c_int64), ("piv", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    """ffsrqr_request_t: one request of the server (device pointers)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("A", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("seed", ctypes.c_uint64), ("U", ctypes.c_void_p),
+                ("ldu", ctypes.c_int64), ("S", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("ldv", ctypes.c_int64), ("piv", ctypes.c_void_p)]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -72,6 +88,32 @@ def _load():
     lib.ffsrqr_launch_count.restype = ctypes.c_int
     lib.ffsrqr_qrcp_static.argtypes = [P, i64, i32, i64, i32, P, P, P, P]
     lib.ffsrqr_qrcp_static.restype = ctypes.c_int
+    lib.ffsrqr_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, P, i32, ctypes.POINTER(Opts), i32,
+                                        ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_batch_create.restype = ctypes.c_int
+    lib.ffsrqr_batch_run.argtypes = [P, P, P, P, P]
+    lib.ffsrqr_batch_run.restype = ctypes.c_int
+    lib.ffsrqr_batch_tune.argtypes = [P, P, P, P, P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    lib.ffsrqr_batch_tune.restype = ctypes.c_int
+    lib.ffsrqr_batch_streams.argtypes = [P]
+    lib.ffsrqr_batch_streams.restype = ctypes.c_int
+    lib.ffsrqr_batch_workspace_offset.argtypes = [P, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(P)]
+    lib.ffsrqr_batch_workspace_offset.restype = ctypes.c_int
+    lib.ffsrqr_batch_destroy.argtypes = [P]
+    lib.ffsrqr_batch_destroy.restype = ctypes.c_int
+    lib.ffsrqr_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, i32, ctypes.POINTER(Opts)]
+    lib.ffsrqr_server_create.restype = ctypes.c_int
+    lib.ffsrqr_server_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(i64)]
+    lib.ffsrqr_server_submit.restype = ctypes.c_int
+    lib.ffsrqr_server_poll.argtypes = [P, i64, ctypes.POINTER(Info), ctypes.POINTER(ctypes.c_double)]
+    lib.ffsrqr_server_poll.restype = ctypes.c_int
+    lib.ffsrqr_server_wait.argtypes = [P, i64, ctypes.POINTER(Info), ctypes.POINTER(ctypes.c_double)]
+    lib.ffsrqr_server_wait.restype = ctypes.c_int
+    lib.ffsrqr_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                        ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_server_stats.restype = ctypes.c_int
+    lib.ffsrqr_server_destroy.argtypes = [P]
+    lib.ffsrqr_server_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -88,6 +130,18 @@ ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
 ffsrqr_phase_times = lib.ffsrqr_phase_times
 ffsrqr_launch_count = lib.ffsrqr_launch_count
 ffsrqr_phase_times_back = lib.ffsrqr_phase_times_back
+ffsrqr_batch_create = lib.ffsrqr_batch_create
+ffsrqr_batch_run = lib.ffsrqr_batch_run
+ffsrqr_batch_tune = lib.ffsrqr_batch_tune
+ffsrqr_batch_streams = lib.ffsrqr_batch_streams
+ffsrqr_batch_workspace_offset = lib.ffsrqr_batch_workspace_offset
+ffsrqr_batch_destroy = lib.ffsrqr_batch_destroy
+ffsrqr_server_create = lib.ffsrqr_server_create
+ffsrqr_server_submit = lib.ffsrqr_server_submit
+ffsrqr_server_poll = lib.ffsrqr_server_poll
+ffsrqr_server_wait = lib.ffsrqr_server_wait
+ffsrqr_server_stats = lib.ffsrqr_server_stats
+ffsrqr_server_destroy = lib.ffsrqr_server_destroy
 ffsrqr_qrcp_static = lib.ffsrqr_qrcp_static
 
 
@@ -193,3 +247,131 @@ def phase_times(plan: "Plan", back: int = 0) -> dict:
     if cnt < 0:
         raise FfsrqrError(f"ffsrqr_phase_times_back returned {cnt}")
     return {PHASES[i]: buf[i] for i in range(cnt)}
+
+
+class Batch:
+    """Many problems of uneven sizes run as one CUDA graph (ffsrqr_batch_*).
+
+    sizes: list of (m, n, k, p).  The workspace is one torch uint8 buffer;
+    outputs() allocates each problem's (U, S, V, piv)."""
+
+    def __init__(self, sizes, mode: int = PLAIN_FP32, streams: int = 4, g: float = 2.0, device=None):
+        import torch
+        self.sizes = [tuple(int(v) for v in sz) for sz in sizes]
+        self.mode = mode
+        self.device = torch.device("cuda" if device is None else device)
+        self.dtype = torch.float64 if mode == FP64 else torch.float32
+        cnt = len(self.sizes)
+        arr = lambda ct, col: (ct * cnt)(*[sz[col] for sz in self.sizes])  # noqa: E731
+        self._m, self._n = arr(ctypes.c_int64, 0), arr(ctypes.c_int64, 1)
+        self._k, self._p = arr(ctypes.c_int32, 2), arr(ctypes.c_int32, 3)
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        opts = Opts(g, 0, 0)
+        opts_p = None
+        if g != 2.0:
+            opts = Opts(g, 4 * max(sz[2] for sz in self.sizes), 0)
+            opts_p = ctypes.byref(opts)
+        _check(lib.ffsrqr_batch_create(ctypes.byref(self._h), cnt, self._m, self._n, self._k, self._p, mode,
+                                       opts_p, streams, ctypes.byref(ws)), "ffsrqr_batch_create")
+        self.workspace = torch.empty(ws.value + 256, dtype=torch.uint8, device=self.device)
+        self._ws_off = (-self.workspace.data_ptr()) % 256
+        self._info = torch.zeros(cnt * ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
+
+    def outputs(self):
+        import torch
+        outs = []
+        for m, n, k, p in self.sizes:
+            outs.append((torch.empty(m, k, dtype=self.dtype, device=self.device),
+                         torch.empty(k, dtype=self.dtype, device=self.device),
+                         torch.empty(n, k, dtype=self.dtype, device=self.device),
+                         torch.empty(n, dtype=torch.int32, device=self.device)))
+        return outs
+
+    def _problems(self, As, outs, seeds):
+        probs = (Problem * len(self.sizes))()
+        for i, (A, (U, S, V, piv)) in enumerate(zip(As, outs)):
+            assert A.is_cuda and A.dtype == self.dtype and A.stride(1) == 1
+            probs[i] = Problem(A.data_ptr(), A.stride(0), seeds[i], U.data_ptr(), U.stride(0), S.data_ptr(),
+                               V.data_ptr(), V.stride(0), piv.data_ptr())
+        return probs
+
+    def run(self, As, outs, seeds=None, stream=None):
+        import torch
+        seeds = seeds or [0] * len(self.sizes)
+        self._probs = self._problems(As, outs, seeds)  # kept alive: the graph was captured with it
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        _check(lib.ffsrqr_batch_run(self._h, self._probs, self.workspace.data_ptr() + self._ws_off,
+                                    ctypes.c_void_p(st.cuda_stream), self._info.data_ptr()), "ffsrqr_batch_run")
+
+    def tune(self, As, outs, seeds=None, stream=None):
+        import torch
+        seeds = seeds or [0] * len(self.sizes)
+        self._probs = self._problems(As, outs, seeds)
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        chosen, ms = ctypes.c_int32(), ctypes.c_float()
+        _check(lib.ffsrqr_batch_tune(self._h, self._probs, self.workspace.data_ptr() + self._ws_off,
+                                     ctypes.c_void_p(st.cuda_stream), self._info.data_ptr(),
+                                     ctypes.byref(chosen), ctypes.byref(ms)), "ffsrqr_batch_tune")
+        return chosen.value, ms.value
+
+    def info(self, i: int) -> dict:
+        sz = ctypes.sizeof(Info)
+        return Info.from_buffer_copy(bytes(self._info[i * sz:(i + 1) * sz].numpy().tobytes())).as_dict()
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.ffsrqr_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+
+class Server:
+    """Request server (ffsrqr_server_*): device memory budget, slots streams."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4):
+        self._h = ctypes.c_void_p()
+        _check(lib.ffsrqr_server_create(ctypes.byref(self._h), budget_bytes, slots, None), "ffsrqr_server_create")
+        self._keep = {}
+
+    def submit(self, A, k: int, p: int, mode: int, out, seed: int = 0) -> int:
+        U, S, V, piv = out
+        m, n = A.shape
+        req = Request(m, n, k, p, mode, 0, A.data_ptr(), A.stride(0), seed, U.data_ptr(), U.stride(0),
+                      S.data_ptr(), V.data_ptr(), V.stride(0), piv.data_ptr())
+        t = ctypes.c_int64()
+        rc = lib.ffsrqr_server_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        if rc != 0:
+            raise FfsrqrError(f"ffsrqr_server_submit returned {rc} ({lib.ffsrqr_status_string(rc).decode()})")
+        self._keep[t.value] = (A, out)  # buffers stay alive until the request finishes
+        return t.value
+
+    def wait(self, ticket: int):
+        info, lat = Info(), ctypes.c_double()
+        rc = lib.ffsrqr_server_wait(self._h, ticket, ctypes.byref(info), ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        _check(rc, "ffsrqr_server_wait")
+        return info.as_dict(), lat.value
+
+    def poll(self, ticket: int):
+        info, lat = Info(), ctypes.c_double()
+        rc = lib.ffsrqr_server_poll(self._h, ticket, ctypes.byref(info), ctypes.byref(lat))
+        if rc == 1:
+            return None
+        self._keep.pop(ticket, None)
+        _check(rc, "ffsrqr_server_poll")
+        return info.as_dict(), lat.value
+
+    def stats(self) -> dict:
+        a, c, q, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(lib.ffsrqr_server_stats(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(q), ctypes.byref(f)),
+               "ffsrqr_server_stats")
+        return {"admitted": a.value, "completed": c.value, "queued": q.value, "arena_free": f.value}
+
+    def close(self):
+        if self._h.value:
+            lib.ffsrqr_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()
+
