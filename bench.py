@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batch", "hosvd", "serving"], default="single",
+                    help="single: one 20000x20000 problem (default); batch: 256 uneven matrices in one graph; "
+                         "hosvd: the three unfoldings of a 400^3 tensor; serving: Poisson request stream")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     return ap.parse_args()
 
 
@@ -313,8 +318,163 @@ def run_ours(a, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# batched and serving workloads (one GPU; not the default line)
+# --------------------------------------------------------------------------
+def _batch_line(a, name, count, ms, roof_bytes, extra):
+    from paper_1803_01982_gb300 import ffsrqr  # noqa: F401
+    peak, src = peaks()
+    t_roof = roof_bytes / (peak * 1e9) * 1e3
+    line = {"metric": METRIC, "value": count * 1000.0 / ms, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "problems_per_step": count},
+            "roofline": {"bound": "hbm", "achieved": roof_bytes / (ms * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": t_roof / ms, "peak_source": src,
+                         "algorithmic_bytes_per_step": roof_bytes, "note": "three reads of every A"}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def _time_batch(a, b, mats, outs):
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        b.run(mats, outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        b.run(mats, outs)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / a.steps
+
+
+def run_batch(a):
+    """256 FP32 matrices, m, n log-uniform in [256, 4096] (n rounded to a
+    multiple of 4), k uniform in [8, 64], p = 10, sigma_j = 0.9^j (rank
+    min(m, n, 256) plus N(0, 1e-6^2) noise): one graph launch per step."""
+    import numpy as np
+    import torch
+
+    from paper_1803_01982_gb300 import ffsrqr, synth
+    rng = np.random.default_rng(4)
+    sizes, mats = [], []
+    for i in range(256):
+        m, n = (int(round(np.exp(rng.uniform(np.log(256), np.log(4096))))) for _ in range(2))
+        n += (-n) % 4
+        k = int(rng.integers(8, 65))
+        r = min(m, n, 256)
+        mats.append(synth.decayed_torch(m, n, 0.9 ** np.arange(r), 1e-6, seed=1000 + i))
+        sizes.append((m, n, k, 10))
+    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    b = ffsrqr.Batch(sizes, mode, streams=4)
+    outs = b.outputs()
+    chosen, tune_ms = b.tune(mats, outs)
+    ms = _time_batch(a, b, mats, outs)
+    roof = sum(12.0 * m * n for m, n, _, _ in sizes)
+    _batch_line(a, f"256 uneven FP32 matrices (m, n in [256, 4096], k in [8, 64], p = 10, sigma_j = 0.9^j), {a.mode}",
+                256, ms, roof, {"autotune": {"streams": chosen, "ms": tune_ms}})
+
+
+def run_hosvd(a):
+    """Tucker/HOSVD factors of a 400^3 FP32 tensor (core 40^3 N(0,1) times
+    three orthonormal 400 x 40 factors, plus N(0, 1e-4^2) noise): rank-40
+    approximations (p = 5) of its three 400 x 160000 unfoldings in one graph.
+    The mode-2 and mode-3 unfoldings are materialised as permuted copies."""
+    import numpy as np
+    import torch
+
+    from paper_1803_01982_gb300 import ffsrqr, synth
+    rng = np.random.default_rng(5)
+    Us = [torch.as_tensor(synth.orthonormal(rng, 400, 40), device="cuda") for _ in range(3)]
+    G = torch.as_tensor(rng.standard_normal((40, 40, 40)), device="cuda")
+    T = torch.einsum("abc,ia,jb,kc->ijk", G, Us[0], Us[1], Us[2])
+    T = T + 1e-4 * torch.randn(T.shape, dtype=T.dtype, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    T = T.float()
+    unf = [T.reshape(400, 160000).contiguous(), T.permute(1, 0, 2).reshape(400, 160000).contiguous(),
+           T.permute(2, 0, 1).reshape(400, 160000).contiguous()]
+    del T
+    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    b = ffsrqr.Batch([(400, 160000, 40, 5)] * 3, mode, streams=3)
+    outs = b.outputs()
+    ms = _time_batch(a, b, unf, outs)
+    _batch_line(a, f"HOSVD factors of a 400^3 FP32 tensor (3 unfoldings 400x160000, k = 40, p = 5), {a.mode}",
+                3, ms, 3 * 12.0 * 400 * 160000, {})
+
+
+def run_serving(a):
+    """Poisson arrivals (mean a.rate per second, a.duration seconds) of
+    truncated-SVD requests like singular-value-thresholding iterates:
+    A = X_L X_R^T + N(0, 1e-3^2), X_L, X_R Gaussian of rank r uniform in
+    [10, 100], m, n log-uniform in [500, 8000] (n a multiple of 4),
+    k = r + 10, p = 10, served under a 120 GB budget with 8 slots.  The
+    matrices come from a pool of 64 generated up front."""
+    import numpy as np
+    import torch
+
+    from paper_1803_01982_gb300 import ffsrqr
+    rng = np.random.default_rng(6)
+    pool = []
+    gen = torch.Generator("cuda").manual_seed(6)
+    for i in range(64):
+        m, n = (int(round(np.exp(rng.uniform(np.log(500), np.log(8000))))) for _ in range(2))
+        n += (-n) % 4
+        r = int(rng.integers(10, 101))
+        XL = torch.randn(m, r, device="cuda", generator=gen)
+        XR = torch.randn(n, r, device="cuda", generator=gen)
+        A = XL @ XR.T + 1e-3 * torch.randn(m, n, device="cuda", generator=gen)
+        pool.append((A, r + 10))
+    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    srv = ffsrqr.Server(120 * (1 << 30), slots=8)
+    # warm the plan cache and the kernels
+    for A, k in pool[:4]:
+        o = (torch.empty(A.shape[0], k, device="cuda"), torch.empty(k, device="cuda"),
+             torch.empty(A.shape[1], k, device="cuda"), torch.empty(A.shape[1], dtype=torch.int32, device="cuda"))
+        srv.wait(srv.submit(A, k, 10, mode, o))
+    gaps = rng.exponential(1.0 / a.rate, size=int(a.rate * a.duration * 1.5) + 10)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < a.duration]
+    lat, pending = [], []
+    t0 = time.perf_counter()
+    for i, ta in enumerate(arrivals):
+        while time.perf_counter() - t0 < ta:
+            # collect finished requests while waiting for the next arrival
+            still = []
+            for t in pending:
+                r = srv.poll(t)
+                if r is None:
+                    still.append(t)
+                else:
+                    lat.append(r[1])
+            pending = still
+            time.sleep(0.0002)
+        A, k = pool[i % len(pool)]
+        o = (torch.empty(A.shape[0], k, device="cuda"), torch.empty(k, device="cuda"),
+             torch.empty(A.shape[1], k, device="cuda"), torch.empty(A.shape[1], dtype=torch.int32, device="cuda"))
+        pending.append(srv.submit(A, k, 10, mode, o))
+    for t in pending:
+        lat.append(srv.wait(t)[1])
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat) * 1e3
+    line = {"metric": "serving latency p50/p99 (ms) and throughput", "value": len(lat) / wall,
+            "unit": "req/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Poisson {a.rate:g} req/s for {a.duration:g} s, m, n in [500, 8000], "
+                                   f"rank 10..100 + noise, k = r + 10, p = 10, 120 GB budget, 8 slots, {a.mode}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "requests": int(len(lat)), "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload != "single" and a.impl == "ours":
+        {"batch": run_batch, "hosvd": run_hosvd, "serving": run_serving}[a.workload](a)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
