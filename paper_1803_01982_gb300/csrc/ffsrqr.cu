@@ -92,7 +92,7 @@ struct ffsrqr_plan_s {
   size_t off_ctl, off_dctl, off_info, off_om, off_bt, off_sel, off_s11, off_cval, off_cidx, off_ccol;
   size_t off_q1, off_w, off_rc1, off_rc2, off_gt, off_r11, off_rinv, off_zt, off_bjt, off_cbt,
       off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
-      off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_part, off_sgnv, off_sgni, off_sgn;
+      off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_qv, off_part, off_sgnv, off_sgni, off_sgn;
   size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
   size_t off_sinv, off_sh, off_sl, off_scr;   // tensor-core small products (FFSRQR_MIXED)
   size_t off_jlog;                            // Jacobi rotation log
@@ -360,7 +360,7 @@ struct WsPtrs {
   int *ctl;
   double *dctl;
   T *om, *bt, *s11, *cval, *ccol, *q1, *gt, *r11, *rinv, *zt, *bjt, *cbt, *r, *bv, *avec, *z, *hpart,
-      *npart, *vp, *rz, *tmp, *yt, *rt, *t1, *mt, *us, *vs, *sgnv, *sgn;
+      *npart, *vp, *rz, *tmp, *yt, *rt, *t1, *mt, *us, *vs, *qv, *sgnv, *sgn;
   int *sel, *cidx, *bi, *sgni;
 };
 
@@ -397,6 +397,7 @@ WsPtrs<T> ws_ptrs(const ffsrqr_plan_s *P, unsigned char *ws) {
   PT(mt, off_mt);
   PT(us, off_us);
   PT(vs, off_vs);
+  PT(qv, off_qv);
   PT(sgnv, off_sgnv);
   PT(sgn, off_sgn);
   PT(sel, off_sel);
@@ -756,12 +757,12 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   {
     const int kk = k + (k & 1);
     const int kp = (int)round_up(k, 16 / (int)sizeof(T));
-    const size_t smem = (size_t)kk * kp * sizeof(T) + (size_t)kk * sizeof(T) + (size_t)kk * sizeof(int) + 64;
+    const size_t smem = ((size_t)kk * kp + 5 * (size_t)kp + kk) * sizeof(T) + (size_t)kk * sizeof(int) + 64;
     CK(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const T eps = (sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16);
     const T tol = (sizeof(T) == 4) ? T(4) * sqrt(T(k)) * eps : T(k) * eps;
     T *jlog = reinterpret_cast<T *>(ws + P->off_jlog);
-    jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, jlog, w.ctl, JAC_MAX_SWEEPS, tol);
+    jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, jlog, w.qv, w.ctl, JAC_MAX_SWEEPS, tol);
     CKL("jacobi_svd");
   }
   MARK(11);
@@ -846,6 +847,7 @@ void layout(ffsrqr_plan_s *P) {
   P->off_mt = take((size_t)k * k * E);
   P->off_us = take((size_t)k * k * E);
   P->off_vs = take((size_t)k * k * E);
+  P->off_qv = take(((size_t)k + 1) * round_up(k, 16 / (int)E) * E);  // reflectors + tau of the QR of M_t^T
   {
     const int kk = k + (k & 1);
     P->off_jlog = take((size_t)JAC_MAX_SWEEPS * (kk - 1) * (kk / 2) * 2 * E);  // Jacobi rotation log
