@@ -92,10 +92,12 @@ struct ffsrqr_plan_s {
   size_t off_ctl, off_dctl, off_info, off_om, off_bt, off_sel, off_s11, off_cval, off_cidx, off_ccol;
   size_t off_q1, off_w, off_rc1, off_rc2, off_gt, off_r11, off_rinv, off_zt, off_bjt, off_cbt,
       off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
-      off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_qv, off_part, off_sgnv, off_sgni, off_sgn;
+      off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_qv, off_qg, off_part, off_sgnv, off_sgni, off_sgn;
   size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
   size_t off_sinv, off_sh, off_sl, off_scr;   // tensor-core small products (FFSRQR_MIXED)
-  size_t off_jlog;                            // Jacobi rotation log
+  int jac_cluster, jac_lpp;                   // blocks of the Jacobi cluster, lanes per pair
+  cudaStream_t side = nullptr;                // forms Q of the small QR while the Jacobi runs
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t off_rowk, off_qk, off_rot, off_rd, off_xinv, off_swpart, off_swbv, off_swbi;  // swap loop
   int swap_grid;
   size_t swap_smem;
@@ -360,7 +362,7 @@ struct WsPtrs {
   int *ctl;
   double *dctl;
   T *om, *bt, *s11, *cval, *ccol, *q1, *gt, *r11, *rinv, *zt, *bjt, *cbt, *r, *bv, *avec, *z, *hpart,
-      *npart, *vp, *rz, *tmp, *yt, *rt, *t1, *mt, *us, *vs, *qv, *sgnv, *sgn;
+      *npart, *vp, *rz, *tmp, *yt, *rt, *t1, *mt, *us, *vs, *qv, *qg, *sgnv, *sgn;
   int *sel, *cidx, *bi, *sgni;
 };
 
@@ -398,6 +400,7 @@ WsPtrs<T> ws_ptrs(const ffsrqr_plan_s *P, unsigned char *ws) {
   PT(us, off_us);
   PT(vs, off_vs);
   PT(qv, off_qv);
+  PT(qg, off_qg);
   PT(sgnv, off_sgnv);
   PT(sgn, off_sgn);
   PT(sel, off_sel);
@@ -559,6 +562,45 @@ int cholqr2_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const
     trmm_upper_kernel<float><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(R2, R1, k, Rout);
     CKL("trmm_upper");
   }
+  return 0;
+}
+
+// Cluster launch of the Jacobi kernel for the plan's (blocks, lanes per pair).
+template <typename T, int LPP>
+cudaError_t launch_jacobi_lpp(cudaStream_t st, int C, int k, const T *X, const T *J, T *U, T *S, T *V, int *ctl,
+                              T tol, bool query, int *clusters) {
+  const JacGeom g = jac_geom(k, C, 16 / (int)sizeof(T));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3((unsigned)round_up((int64_t)g.npair * LPP, 32));
+  cfg.dynamicSmemBytes = jac_cluster_smem(k, C, sizeof(T));
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query) return cudaOccupancyMaxActiveClusters(clusters, jacobi_cluster_kernel<T, LPP>, &cfg);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<T, LPP>, X, J, k, U, S, V, ctl, (int)JAC_MAX_SWEEPS, tol);
+}
+
+template <typename T>
+cudaError_t launch_jacobi_any(cudaStream_t st, int C, int lpp, int k, const T *X, const T *J, T *U, T *S, T *V,
+                              int *ctl, T tol, bool query, int *clusters) {
+  switch (lpp) {
+    case 2: return launch_jacobi_lpp<T, 2>(st, C, k, X, J, U, S, V, ctl, tol, query, clusters);
+    case 4: return launch_jacobi_lpp<T, 4>(st, C, k, X, J, U, S, V, ctl, tol, query, clusters);
+    default: return launch_jacobi_lpp<T, 8>(st, C, k, X, J, U, S, V, ctl, tol, query, clusters);
+  }
+}
+
+template <typename T>
+int launch_jacobi(cudaStream_t st, const ffsrqr_plan_s *P, const T *X, const T *J, T *U, T *S, T *V, int *ctl,
+                  T tol) {
+  CK(launch_jacobi_any<T>(st, P->jac_cluster, P->jac_lpp, P->k, X, J, U, S, V, ctl, tol, false, nullptr));
+  ++g_launches;
   return 0;
 }
 
@@ -755,15 +797,22 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.t1, k, false, w.rz, k, false, w.mt, k))) return rc;
   MARK(10);
   {
-    const int kk = k + (k & 1);
-    const int kp = (int)round_up(k, 16 / (int)sizeof(T));
-    const size_t smem = ((size_t)kk * kp + 5 * (size_t)kp + kk) * sizeof(T) + (size_t)kk * sizeof(int) + 64;
-    CK(cudaFuncSetAttribute(jacobi_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // M_t^T = Q R: X = R^T to t1 and the reflectors to qv; Q (to qg) is formed
+    // on the plan's side stream while the cluster Jacobi runs on [X; I]; then
+    // V_s = Q J (J to t1, which the Jacobi no longer needs once loaded)
+    const size_t qsmem = precond_qr_smem(k, sizeof(T));
+    precond_qr_r_kernel<T><<<1, 1024, qsmem, st>>>(w.mt, k, w.t1, w.qv);
+    CKL("precond_qr_r");
+    CK(cudaEventRecord(P->ev_fork, st));
+    CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    precond_qr_q_kernel<T><<<1, 1024, qsmem, P->side>>>(k, w.qv, w.qg);
+    CKL("precond_qr_q");
+    CK(cudaEventRecord(P->ev_join, P->side));
     const T eps = (sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16);
     const T tol = (sizeof(T) == 4) ? T(4) * sqrt(T(k)) * eps : T(k) * eps;
-    T *jlog = reinterpret_cast<T *>(ws + P->off_jlog);
-    jacobi_svd_kernel<T><<<2, 1024, smem, st>>>(w.mt, k, w.us, S, w.vs, jlog, w.qv, w.ctl, JAC_MAX_SWEEPS, tol);
-    CKL("jacobi_svd");
+    if ((rc = launch_jacobi<T>(st, P, w.t1, (const T *)nullptr, w.us, S, w.t1, w.ctl, tol))) return rc;
+    CK(cudaStreamWaitEvent(st, P->ev_join, 0));
+    if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.qg, k, true, w.t1, k, true, w.vs, k))) return rc;
   }
   MARK(11);
   // a11: U = Q_t U_s, V = V' V_s, sign rule
@@ -848,10 +897,7 @@ void layout(ffsrqr_plan_s *P) {
   P->off_us = take((size_t)k * k * E);
   P->off_vs = take((size_t)k * k * E);
   P->off_qv = take(((size_t)k + 1) * round_up(k, 16 / (int)E) * E);  // reflectors + tau of the QR of M_t^T
-  {
-    const int kk = k + (k & 1);
-    P->off_jlog = take((size_t)JAC_MAX_SWEEPS * (kk - 1) * (kk / 2) * 2 * E);  // Jacobi rotation log
-  }
+  P->off_qg = take((size_t)k * k * E);  // Q of the QR of M_t^T
   P->off_rowk = take((size_t)n * E);
   P->off_qk = take((size_t)m * E);
   P->off_rot = take((size_t)2 * k * E);
@@ -897,6 +943,51 @@ void layout(ffsrqr_plan_s *P) {
   item(6, P->off_tmp, m, k, ldk);
   item(7, P->off_r, n, 1, 1);
   item(8, P->off_mt, k, k, k);
+}
+
+// The QR kernels of the small SVD and the shape of the Jacobi cluster: the
+// first (blocks, lanes per pair) of the list below whose slab fits the
+// per-lane registers, whose blocks stay within 512 threads and whose cluster
+// the device can hold.
+template <typename T>
+int plan_jacobi(ffsrqr_plan_s *P) {
+  const int k = P->k;
+  const int vn = 16 / (int)sizeof(T);
+  const size_t qsmem = precond_qr_smem(k, sizeof(T));
+  if (qsmem > (size_t)P->smem_optin) return FFSRQR_STATUS_UNSUPPORTED;
+  // the caps are per kernel, shared by every plan: set them to the device
+  // maximum less the kernel's static shared memory
+  {
+    const void *fns[5] = {(const void *)precond_qr_r_kernel<T>, (const void *)precond_qr_q_kernel<T>,
+                          (const void *)jacobi_cluster_kernel<T, 2>, (const void *)jacobi_cluster_kernel<T, 4>,
+                          (const void *)jacobi_cluster_kernel<T, 8>};
+    for (const void *fn : fns) {
+      cudaFuncAttributes fa;
+      CK(cudaFuncGetAttributes(&fa, fn));
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              P->smem_optin - (int)fa.sharedSizeBytes));
+    }
+  }
+  P->jac_cluster = 0;
+  P->jac_lpp = 0;
+  const int cand[7][2] = {{8, 4}, {4, 4}, {8, 2}, {2, 4}, {2, 8}, {4, 8}, {8, 8}};
+  for (int ci = 0; ci < 7 && !P->jac_cluster; ++ci) {
+    const int C = cand[ci][0], lpp = cand[ci][1];
+    const JacGeom g = jac_geom(k, C, vn);
+    if (cdiv(g.hb / vn, lpp) > JAC_NVL) continue;
+    if (round_up((int64_t)g.npair * lpp, 32) > 512) continue;
+    if (jac_cluster_smem(k, C, sizeof(T)) + 1024 > (size_t)P->smem_optin) continue;
+    int nc = 0;
+    if (launch_jacobi_any<T>(nullptr, C, lpp, k, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, T(0), true,
+                             &nc) == cudaSuccess &&
+        nc >= 1) {
+      P->jac_cluster = C;
+      P->jac_lpp = lpp;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
+  return P->jac_cluster ? 0 : FFSRQR_STATUS_UNSUPPORTED;
 }
 
 template <typename T>
@@ -976,7 +1067,15 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
     return FFSRQR_STATUS_CUDA;
   }
   int rc = (elem == 8) ? plan_qrcp<double>(P) : plan_qrcp<float>(P);
+  if (!rc) rc = (elem == 8) ? plan_jacobi<double>(P) : plan_jacobi<float>(P);
+  if (!rc && !(cuda_ok(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking), "cudaStreamCreate") &&
+               cuda_ok(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming), "cudaEventCreate") &&
+               cuda_ok(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming), "cudaEventCreate")))
+    rc = FFSRQR_STATUS_CUDA;
   if (rc) {
+    if (P->side) cudaStreamDestroy(P->side);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
     delete P;
     return rc;
   }
@@ -989,7 +1088,7 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
         ok = cuda_ok(cudaEventCreate(&P->ev_tc[e][i / 2][i % 2]), "cudaEventCreate");
     }
     if (!ok) {
-      delete P;
+      ffsrqr_destroy(P);
       return FFSRQR_STATUS_CUDA;
     }
     P->ev_ok = true;
@@ -1032,6 +1131,12 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
 
 int ffsrqr_destroy(ffsrqr_plan_t plan) {
   if (!plan) return -1;
+  if (plan->side) {
+    cudaStreamSynchronize(plan->side);
+    cudaStreamDestroy(plan->side);
+  }
+  if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+  if (plan->ev_join) cudaEventDestroy(plan->ev_join);
   if (plan->ev_ok) {
     for (int e = 0; e < 2; ++e) {
       for (int i = 0; i < 13; ++i) cudaEventDestroy(plan->ev[e][i]);

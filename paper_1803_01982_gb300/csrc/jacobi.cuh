@@ -1,29 +1,41 @@
 // jacobi.cuh -- SVD of the small k x k factor M of tmp (Alg. 9, lines 4-5) by
 // one-sided (Hestenes) Jacobi, preconditioned by a QR factorisation, on a
-// 2-CTA thread-block cluster.
+// thread-block cluster.
 //
 //   M^T = Q R (Householder, no pivoting), X = R^T, X J = W diag(sigma):
 //   pairs of columns of X (rows of R) are rotated until every pair is
-//   orthogonal to within tol * ||x_p|| ||x_q||; J accumulates the rotations.
-//   Then R = J diag(sigma) W^T and M = W diag(sigma) (Q J)^T, i.e. U = W
-//   normalised and V = Q J.  The rows of R are graded like the singular
-//   values, which makes the sweeps converge in about a third fewer sweeps
-//   than on M^T itself (the QR preconditioning of one-sided Jacobi of Drmac
-//   and Veselic, without the column pivoting, which gains nothing here).
+//   orthogonal to within tol * ||x_p|| ||x_q||; J, started at Q, accumulates
+//   the rotations.  Then M^T = (Q J) diag(sigma) W^T, i.e. U = W normalised
+//   and V = Q J.  The rows of R are graded like the singular values, which
+//   makes the sweeps converge in about a third fewer sweeps than on M^T
+//   itself (the QR preconditioning of one-sided Jacobi of Drmac and Veselic,
+//   without the column pivoting, which gains nothing here).
 //
-// Rank 0 holds M^T (column-major, padded stride) in shared memory, factors it
-// in place, writes the Householder vectors to global memory and publishes
-// them, transposes R into X and runs the parallel round-robin ordering: kk/2
-// disjoint pairs per round, every pair meets once per sweep of kk-1 rounds.
-// Each pair is handled by 8 lanes (four pairs per warp) with 16-byte
-// shared-memory accesses.  The (cos, sin) of every round go to a rotation log
-// in global memory; every JAC_GROUP rounds one gpu-scope release publishes the
-// progress counter.  Rank 1 forms Q from the published reflectors while rank
-// 0 sweeps, then applies the logged rounds to it as they are published
-// (acquire loads of the counter), so the two CTAs never wait on each other per
-// round.  After convergence (a sweep without rotations) sigma_j = ||x_j||, the
-// ranks of the sorted order go to rank 1 through DSMEM, and both write their
-// outputs.  All waits are bounded.
+// The QR runs in two single-block kernels (R and the reflectors; then Q).
+// The sweeps run on a cluster of C blocks (C = 2, 4 or 8).  The rows of the
+// stacked matrix [X; J] (2 kp rows, kk columns) are split into C slabs, one
+// per block, each held column-major in shared memory.  One round of the
+// parallel round-robin ordering (kk/2 disjoint pairs, every pair meets once
+// per sweep of kk - 1 rounds) is, in every block at once:
+//   1. the LPP lanes of pair i (2 or 4; few lanes per pair keep the warps,
+//      and the per-warp work of a round, few) load their slices of columns p
+//      and q of the slab into registers and form the partial sums of
+//      ||x_p||^2, ||x_q||^2 and x_p . x_q over the X rows of the slab;
+//   2. the partials go to the block's own shared memory (slot [round
+//      parity][pair]);
+//   3. one cluster barrier;
+//   4. every block reads the partials of the blocks holding X rows through
+//      distributed shared memory and adds them in block order, so all blocks
+//      take the same rotation (cos, sin) and the same convergence decisions;
+//      it rotates its registers and stores them back;
+//   5. one block barrier (the next round pairs the columns differently).
+// The slab of a block is 1/C of the matrix, so the shared-memory traffic of a
+// round (one read and one write of the slab) and its latency shrink with C.
+// After a sweep without rotations, sigma_c = ||x_c|| (one more exchange of
+// partial norms), the columns are ranked by descending sigma and each block
+// writes its rows of U (from X) and V (from J).  There are no spin-waits: all
+// blocks run the same sequence of barriers, the rounds of a sweep being fixed
+// in number and the end of the sweeps being block 0's decision, broadcast.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -34,39 +46,26 @@ namespace ffq {
 
 namespace cg = cooperative_groups;
 
-constexpr int JAC_PPW = 4;      // pairs per warp, 8 lanes each (kk/2 <= 32 * JAC_PPW)
-constexpr int JAC_GROUP = 16;   // rounds per published progress step
 constexpr int JAC_MAX_SWEEPS = 40;
+constexpr int JAC_NVL = 8;      // 16-byte vectors per lane per column of a slab
 
 // Round-robin pairing (circle method): kk players, player kk-1 fixed.
 __device__ __forceinline__ void rr_pair(int t, int i, int kk, int &p, int &q) {
-  const int n1 = kk - 1;
+  const int n1 = kk - 1;  // 0 <= t < n1, 0 <= i < kk / 2
   if (i == 0) {
-    p = t % n1;
+    p = t;
     q = n1;
   } else {
-    p = (t + i) % n1;
-    q = (t - i + n1) % n1;
+    p = t + i;
+    if (p >= n1) p -= n1;
+    q = t - i;
+    if (q < 0) q += n1;
   }
   if (p > q) {
     const int x = p;
     p = q;
     q = x;
   }
-}
-
-__device__ __forceinline__ unsigned long long jac_now() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ int jac_ld_acquire(const int *p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void jac_st_release(int *p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // 16-byte vector of T (4 floats or 2 doubles) in shared memory.
@@ -97,25 +96,6 @@ __device__ __forceinline__ void st16(T *p, const Vec16<T> &r) {
   else *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
 }
 
-// Rotate columns p, q of a column-major shared matrix (stride kp) by (cs, sn);
-// the 8 lanes g8 = 0..7 of a group cover the nv 16-byte vectors of a column.
-template <typename T>
-__device__ __forceinline__ void rotate_cols(T *Mat, int kp, int nv, int p, int q, T cs, T sn, int g8) {
-  constexpr int VN = Vec16<T>::N;
-  T *mp = Mat + (size_t)p * kp, *mq = Mat + (size_t)q * kp;
-  for (int v = g8; v < nv; v += 8) {
-    const Vec16<T> x = ld16(mp + v * VN), y = ld16(mq + v * VN);
-    Vec16<T> xo, yo;
-#pragma unroll
-    for (int u = 0; u < VN; ++u) {
-      xo.v[u] = cs * x.v[u] - sn * y.v[u];
-      yo.v[u] = sn * x.v[u] + cs * y.v[u];
-    }
-    st16(mp + v * VN, xo);
-    st16(mq + v * VN, yo);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // The preconditioning QR, M^T = Q R = H_0 H_1 ... H_{k-1} R.
 //
@@ -132,15 +112,32 @@ __device__ __forceinline__ void hh_apply_group(const T *v, T tau, int q0, int nq
   constexpr int VN = Vec16<T>::N;
   const int lane = threadIdx.x & 31;
   T w[NC];
+  if constexpr (sizeof(T) == 4) {  // packed pairs (f32x2)
+    float2 w2[NC];
 #pragma unroll
-  for (int u = 0; u < NC; ++u) w[u] = T(0);
-  for (int q = q0 + lane; q < nq; q += 32) {
-    const Vec16<T> vv = ld16(v + q * VN);
+    for (int u = 0; u < NC; ++u) w2[u] = make_float2(0.f, 0.f);
+    for (int q = q0 + lane; q < nq; q += 32) {
+      const float4 vv = *reinterpret_cast<const float4 *>(v + q * VN);
+      const float2 vl = make_float2(vv.x, vv.y), vh = make_float2(vv.z, vv.w);
 #pragma unroll
-    for (int u = 0; u < NC; ++u) {
-      const Vec16<T> xx = ld16(src + u * ld + q * VN);
+      for (int u = 0; u < NC; ++u) {
+        const float4 xx = *reinterpret_cast<const float4 *>(src + u * ld + q * VN);
+        w2[u] = __ffma2_rn(vh, make_float2(xx.z, xx.w), __ffma2_rn(vl, make_float2(xx.x, xx.y), w2[u]));
+      }
+    }
 #pragma unroll
-      for (int e = 0; e < VN; ++e) w[u] = fma(vv.v[e], xx.v[e], w[u]);
+    for (int u = 0; u < NC; ++u) w[u] = w2[u].x + w2[u].y;
+  } else {
+#pragma unroll
+    for (int u = 0; u < NC; ++u) w[u] = T(0);
+    for (int q = q0 + lane; q < nq; q += 32) {
+      const Vec16<T> vv = ld16(v + q * VN);
+#pragma unroll
+      for (int u = 0; u < NC; ++u) {
+        const Vec16<T> xx = ld16(src + u * ld + q * VN);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) w[u] = fma(vv.v[e], xx.v[e], w[u]);
+      }
     }
   }
 #pragma unroll
@@ -148,15 +145,32 @@ __device__ __forceinline__ void hh_apply_group(const T *v, T tau, int q0, int nq
 #pragma unroll
     for (int u = 0; u < NC; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
   }
-  for (int q = q0 + lane; q < nq; q += 32) {
-    const Vec16<T> vv = ld16(v + q * VN);
+  if constexpr (sizeof(T) == 4) {
+    float2 m2[NC];
 #pragma unroll
-    for (int u = 0; u < NC; ++u) {
-      const Vec16<T> xx = ld16(src + u * ld + q * VN);
-      Vec16<T> r;
+    for (int u = 0; u < NC; ++u) m2[u] = make_float2(-tau * w[u], -tau * w[u]);
+    for (int q = q0 + lane; q < nq; q += 32) {
+      const float4 vv = *reinterpret_cast<const float4 *>(v + q * VN);
+      const float2 vl = make_float2(vv.x, vv.y), vh = make_float2(vv.z, vv.w);
 #pragma unroll
-      for (int e = 0; e < VN; ++e) r.v[e] = fma(-tau * w[u], vv.v[e], xx.v[e]);
-      st16(dst + u * ld + q * VN, r);
+      for (int u = 0; u < NC; ++u) {
+        const float4 xx = *reinterpret_cast<const float4 *>(src + u * ld + q * VN);
+        const float2 rl = __ffma2_rn(m2[u], vl, make_float2(xx.x, xx.y));
+        const float2 rh = __ffma2_rn(m2[u], vh, make_float2(xx.z, xx.w));
+        *reinterpret_cast<float4 *>(dst + u * ld + q * VN) = make_float4(rl.x, rl.y, rh.x, rh.y);
+      }
+    }
+  } else {
+    for (int q = q0 + lane; q < nq; q += 32) {
+      const Vec16<T> vv = ld16(v + q * VN);
+#pragma unroll
+      for (int u = 0; u < NC; ++u) {
+        const Vec16<T> xx = ld16(src + u * ld + q * VN);
+        Vec16<T> r;
+#pragma unroll
+        for (int e = 0; e < VN; ++e) r.v[e] = fma(-tau * w[u], vv.v[e], xx.v[e]);
+        st16(dst + u * ld + q * VN, r);
+      }
     }
   }
 }
@@ -294,199 +308,331 @@ __device__ void precond_qr_q(T *A, int k, int kp, T *vb0, T *vb1, T *hb0, T *hb1
   __syncthreads();
 }
 
-// M: k x k row-major.  Uout, Vout: k x k row-major (columns in descending
-// order of Sout).  qv: k * kp + k scratch (reflectors and tau of the QR).
-// log: [JAC_MAX_SWEEPS * (kk-1)][kk/2] pairs of (cos, sin).  ctl[CTL_JAC_PROGRESS]
-// (rounds published) and ctl[CTL_JAC_TOTAL] (total rounds, -1 while running)
-// must be 0 and -1 on entry.
+
+// R of M^T and the reflectors: X = R^T to Xg (column-major, X(r, c) at
+// Xg[c * k + r]), reflectors and tau to qv (k * kp + k).  One block.
 template <typename T>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
-    jacobi_svd_kernel(const T *__restrict__ Min, int k, T *__restrict__ Uout, T *__restrict__ Sout,
-                      T *__restrict__ Vout, T *__restrict__ rlog, T *__restrict__ qv, int *ctl, int max_sweeps,
-                      T tol) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned rank = cluster.block_rank();
-  const int kk = k + (k & 1);
-  const int npair = kk / 2;
+__global__ void __launch_bounds__(1024) precond_qr_r_kernel(const T *__restrict__ M, int k, T *__restrict__ Xg,
+                                                             T *__restrict__ qv) {
   constexpr int VN = Vec16<T>::N;
-  const int kp = (k + VN - 1) / VN * VN;  // padded column stride (16-byte aligned columns)
-  const int nv = kp / VN;                 // vectors per column
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Mat = reinterpret_cast<T *>(smem_raw);      // column c at Mat[c*kp], rows >= k zero
-  T *vb0 = Mat + (size_t)kk * kp;                 // QR buffers: 4 vectors of kp, tau [kp]
-  T *vb1 = vb0 + kp, *hb0 = vb1 + kp, *hb1 = hb0 + kp, *tau = hb1 + kp;
-  T *sig = tau + kp;                              // [kk]
-  int *rnk = reinterpret_cast<int *>(sig + kk);   // [kk]
-  __shared__ int s_rot, s_fail, s_avail, s_tot;
+  const int kp = (k + VN - 1) / VN * VN;
+  T *A = reinterpret_cast<T *>(smem_raw);  // k columns of kp
+  T *vb0 = A + (size_t)k * kp, *vb1 = vb0 + kp, *tau = vb1 + kp;
+  for (int e = threadIdx.x; e < k * kp; e += blockDim.x) {
+    const int c = e / kp, r = e - c * kp;
+    A[e] = (r < k) ? M[(size_t)c * k + r] : T(0);  // column c of M^T = row c of M
+  }
+  __syncthreads();
+  precond_qr_r(A, k, kp, vb0, vb1, tau, qv);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int c = e / k, r = e - c * k;
+    Xg[e] = A[(size_t)c * kp + r];
+  }
+}
+
+// Q (column-major, Q(t, c) at Qg[c * k + t]) from the reflectors in qv.
+// One block.
+template <typename T>
+__global__ void __launch_bounds__(1024) precond_qr_q_kernel(int k, const T *__restrict__ qv, T *__restrict__ Qg) {
+  constexpr int VN = Vec16<T>::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kp = (k + VN - 1) / VN * VN;
+  T *A = reinterpret_cast<T *>(smem_raw);
+  T *vb0 = A + (size_t)k * kp, *vb1 = vb0 + kp, *hb0 = vb1 + kp, *hb1 = hb0 + kp, *tau = hb1 + kp;
+  precond_qr_q(A, k, kp, vb0, vb1, hb0, hb1, tau, qv);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int c = e / k, t = e - c * k;
+    Qg[e] = A[(size_t)c * kp + t];
+  }
+}
+
+// Shared-memory bytes of the two QR kernels.
+inline size_t precond_qr_smem(int k, size_t elem) {
+  const size_t kp = (size_t)round_up(k, 16 / (int64_t)elem);
+  return ((size_t)k * kp + 5 * kp) * elem;
+}
+
+// Rotation (cs, sn) that makes columns p, q orthogonal (Rutishauser's
+// formulas): zeta = (be - al) / (2 ga), t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)), cs = 1 / sqrt(1 + t^2), sn = cs t.  No rotation (sn = 0)
+// when |ga| <= tol sqrt(al be).  In single precision t only steers the
+// convergence, so it is formed with the approximate reciprocal and
+// reciprocal square root; cs is refined by one Newton step for 1/sqrt(x),
+// y <- y (3 - x y^2) / 2, so that cs^2 + sn^2 = 1 to rounding and the
+// rotation stays orthogonal.
+template <typename T>
+__device__ __forceinline__ void jac_rotation(T al, T be, T ga, T tol, T &cs, T &sn) {
+  cs = T(1);
+  sn = T(0);
+  if (!(ga != T(0) && fabs(ga) > tol * sqrt(al * be))) return;
+  if constexpr (sizeof(T) == 4) {
+    const float zeta = __fdividef(be - al, 2.f * ga);
+    const float a = fabsf(zeta);
+    float root = a;  // sqrt(1 + a^2), = a to rounding for a >= 2^30
+    if (a < 1073741824.f) {
+      const float x = fmaf(a, a, 1.f);
+      root = x * rsqrtf(x);
+    }
+    const float t = copysignf(__fdividef(1.f, a + root), zeta);
+    const float x = fmaf(t, t, 1.f);
+    float y = rsqrtf(x);
+    y = y * fmaf(-0.5f * x, y * y, 1.5f);
+    cs = y;
+    sn = y * t;
+  } else {
+    const T zeta = (be - al) / (T(2) * ga);
+    const T tt = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    cs = T(1) / sqrt(T(1) + tt * tt);
+    sn = cs * tt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cluster Jacobi.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct JacPart {
+  T al, be, ga, pad;
+};
+
+// Geometry of the slabs (host and device).
+struct JacGeom {
+  int kk, kp, npair, hb, nvx_ctas;
+};
+__host__ __device__ inline JacGeom jac_geom(int k, int C, int VN) {
+  JacGeom g;
+  g.kk = k + (k & 1);
+  g.npair = g.kk / 2;
+  g.kp = (k + VN - 1) / VN * VN;
+  const int nr = 2 * g.kp;                                  // rows of [X; J]
+  g.hb = ((nr + C - 1) / C + VN - 1) / VN * VN;             // slab height, whole vectors
+  g.nvx_ctas = (g.kp + g.hb - 1) / g.hb;                    // blocks holding rows of X
+  return g;
+}
+inline size_t jac_cluster_smem(int k, int C, size_t elem) {
+  const JacGeom g = jac_geom(k, C, 16 / (int)elem);
+  return (size_t)g.kk * g.hb * elem + 2 * (size_t)g.npair * sizeof(JacPart<double>) +
+         (size_t)g.kk * elem + (size_t)g.kk * sizeof(int) + 64;
+}
+
+// Xin: X (column-major, X(r, c) at Xin[c * k + r]); Jin: J_0 (same layout) or
+// NULL for the identity.  Uout, Vout: k x k row-major, columns in descending
+// order of Sout.  LPP lanes share a pair (blockDim = kk/2 * LPP rounded up to
+// whole warps, at most 512), each holding up to JAC_NVL 16-byte vectors of
+// each of the two columns of the slab.
+template <typename T, int LPP>
+__global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict__ Xin, const T *__restrict__ Jin,
+                                                              int k, T *__restrict__ Uout, T *__restrict__ Sout,
+                                                              T *__restrict__ Vout, int *ctl, int max_sweeps, T tol) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  constexpr int VN = Vec16<T>::N;
+  const JacGeom g = jac_geom(k, C, VN);
+  const int kk = g.kk, kp = g.kp, npair = g.npair, hb = g.hb, nxc = g.nvx_ctas;
+  const int r0 = rank * hb;                               // first stacked row of this slab
+  const int nvec = max(0, min(hb, 2 * kp - r0)) / VN;     // vectors per column in the slab
+  const int nvx = max(0, min(nvec, (kp - r0) / VN));      // of which rows of X
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);                           // column c at S[c * hb]
+  JacPart<T> *part = reinterpret_cast<JacPart<T> *>(
+      smem_raw + (((size_t)kk * hb * sizeof(T) + 15) & ~(size_t)15));  // [2][npair]: this block's partials
+  T *sig = reinterpret_cast<T *>(part + 2 * (size_t)npair);         // [kk]
+  int *rnk = reinterpret_cast<int *>(sig + kk);                     // [kk]
+  __shared__ int s_rot, s_done;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int g8 = lane & 7;
-  int *progress = ctl + CTL_JAC_PROGRESS;
-  int *total = ctl + CTL_JAC_TOTAL;
+  const int gl = lane % LPP;  // lane within the pair's group
   if (max_sweeps > JAC_MAX_SWEEPS) max_sweeps = JAC_MAX_SWEEPS;
 
-  for (int e = threadIdx.x; e < kk * kp; e += blockDim.x) {
-    const int c = e / kp, r = e - c * kp;
-    // rank 0: M^T (column c = row c of M); rank 1: zeros (Q is formed below)
-    Mat[e] = (rank == 0 && c < k && r < k) ? Min[(size_t)c * k + r] : T(0);
+  // the slab: stacked rows r0 .. r0 + hb - 1 of [X; J] (X padded to kp rows)
+  for (int e = threadIdx.x; e < kk * hb; e += blockDim.x) {
+    const int c = e / hb, gr = r0 + (e - c * hb);
+    T v = T(0);
+    if (c < k) {
+      if (gr < kp) {
+        if (gr < k) v = Xin[(size_t)c * k + gr];
+      } else if (gr - kp < k) {
+        const int jr = gr - kp;
+        v = Jin ? Jin[(size_t)c * k + jr] : ((jr == c) ? T(1) : T(0));
+      }
+    }
+    S[e] = v;
   }
-  if (threadIdx.x == 0) {
-    s_rot = 0;
-    s_fail = 0;
-  }
+  if (threadIdx.x == 0) s_rot = 0;
   if (rank == 0 && threadIdx.x < 16) ctl[CTL_SWEEP_ROT0 + threadIdx.x] = 0;
   __syncthreads();
+  cluster.sync();  // every block has started before any block reads another's shared memory
 
-  if (rank == 0) {
-    precond_qr_r(Mat, k, kp, vb0, vb1, tau, qv);
-    if (threadIdx.x == 0) jac_st_release(ctl + CTL_JAC_QR, 1);  // the barrier ordered every write of qv
-    int round = 0;
-    int sweeps = 0;
-    bool done = false;
-    for (; sweeps < max_sweeps && !done; ++sweeps) {
-      for (int t = 0; t < kk - 1; ++t, ++round) {
-        const int i = wid * JAC_PPW + (lane >> 3);
-        int p = -1, q = -1;
-        if (i < npair) rr_pair(t, i, kk, p, q);
-        T al = T(0), be = T(0), ga = T(0);
-        if (p >= 0) {
-          const T *mp = Mat + (size_t)p * kp, *mq = Mat + (size_t)q * kp;
-          for (int v = g8; v < nv; v += 8) {
-            const Vec16<T> x = ld16(mp + v * VN), y = ld16(mq + v * VN);
+  const int i = threadIdx.x / LPP;
+  int round = 0, sweeps = 0;
+  bool done = false;
+  for (; sweeps < max_sweeps && !done; ++sweeps) {
+    int nrot = 0;  // rotations of this sweep counted by this thread (one lane per pair)
+    for (int t = 0; t < kk - 1; ++t, ++round) {
+      int p = -1, q = -1;
+      if (i < npair) rr_pair(t, i, kk, p, q);
+      Vec16<T> xr[JAC_NVL], yr[JAC_NVL];
+      T al = T(0), be = T(0), ga = T(0);
+      float2 a2 = make_float2(0.f, 0.f), b2 = a2, g2 = a2;  // packed partial sums (single precision)
+      if (p >= 0) {
+        const T *sp = S + (size_t)p * hb, *sq = S + (size_t)q * hb;
 #pragma unroll
-            for (int u = 0; u < VN; ++u) {
-              al = fma(x.v[u], x.v[u], al);
-              be = fma(y.v[u], y.v[u], be);
-              ga = fma(x.v[u], y.v[u], ga);
+        for (int l = 0; l < JAC_NVL; ++l) {
+          if (LPP * l >= nvec) break;  // uniform: no issue slots for the unused tail
+          const int v = gl + LPP * l;
+          if (v < nvec) {
+            xr[l] = ld16(sp + v * VN);
+            yr[l] = ld16(sq + v * VN);
+            if (v < nvx) {
+              if constexpr (sizeof(T) == 4) {  // packed pairs (f32x2)
+                const float2 xl = make_float2(xr[l].v[0], xr[l].v[1]), xh = make_float2(xr[l].v[2], xr[l].v[3]);
+                const float2 yl = make_float2(yr[l].v[0], yr[l].v[1]), yh = make_float2(yr[l].v[2], yr[l].v[3]);
+                a2 = __ffma2_rn(xh, xh, __ffma2_rn(xl, xl, a2));
+                b2 = __ffma2_rn(yh, yh, __ffma2_rn(yl, yl, b2));
+                g2 = __ffma2_rn(xh, yh, __ffma2_rn(xl, yl, g2));
+              } else {
+#pragma unroll
+                for (int u = 0; u < VN; ++u) {
+                  al = fma(xr[l].v[u], xr[l].v[u], al);
+                  be = fma(yr[l].v[u], yr[l].v[u], be);
+                  ga = fma(xr[l].v[u], yr[l].v[u], ga);
+                }
+              }
             }
           }
         }
+      }
+      if constexpr (sizeof(T) == 4) {
+        al = a2.x + a2.y;
+        be = b2.x + b2.y;
+        ga = g2.x + g2.y;
+      }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        T cs = T(1), sn = T(0);
-        if (p >= 0 && ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
-          const T zeta = (be - al) / (T(2) * ga);
-          const T tt = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          cs = T(1) / sqrt(T(1) + tt * tt);
-          sn = cs * tt;
-        }
-        if (sn != T(0)) rotate_cols(Mat, kp, nv, p, q, cs, sn, g8);
-        if (g8 == 0 && i < npair) {
-          T *e = rlog + ((size_t)round * npair + i) * 2;
-          e[0] = cs;
-          e[1] = sn;
-          if (sn != T(0)) atomicAdd(&s_rot, 1);
-        }
-        __syncthreads();
-        if ((round + 1) % JAC_GROUP == 0 && threadIdx.x == 0) {
-          // publish the rounds so far (the barrier above ordered every warp's log writes)
-          asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(progress), "r"(JAC_GROUP) : "memory");
-        }
+      for (int o = LPP / 2; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
       }
-      done = (s_rot == 0);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        if (sweeps < 16) ctl[CTL_SWEEP_ROT0 + sweeps] = s_rot;
-        s_rot = 0;
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      ctl[CTL_JACOBI_SWEEPS] = sweeps;
-      jac_st_release(total, round);  // ordered after every log write by the barriers above
-    }
-    // sigma and the ranks of the descending order
-    for (int c = wid; c < kk; c += nwarp) {
-      T acc = T(0);
-      if (c < k)
-        for (int r = lane; r < k; r += 32) acc = fma(Mat[(size_t)c * kp + r], Mat[(size_t)c * kp + r], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) sig[c] = sqrt(acc);
-    }
-    __syncthreads();
-    int *rnk1 = cluster.map_shared_rank(rnk, 1);
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      const T sc = sig[c];
-      int rk = 0;
-      for (int d = 0; d < k; ++d) {
-        const T sd = sig[d];
-        rk += (sd > sc) || (sd == sc && d < c);
-      }
-      rnk[c] = rk;
-      rnk1[c] = rk;
-    }
-  } else {
-    // rank 1: Q from the published reflectors, then the published rounds of the log applied to it
-    if (threadIdx.x == 0) {
-      const unsigned long long t0 = jac_now();
-      unsigned spins = 0;
-      while (jac_ld_acquire(ctl + CTL_JAC_QR) == 0) {
-        if ((++spins & 255) == 0 && jac_now() - t0 > 1000000000ull) {
-          s_fail = 1;
-          break;
+      const int par = round & 1;
+      if (p >= 0 && rank < nxc && gl == 0) part[(size_t)par * npair + i] = JacPart<T>{al, be, ga, T(0)};
+      cluster.sync();
+      if (p >= 0) {
+        // the partials of the blocks holding X rows, added in block order:
+        // the same sums, hence the same rotations, in every block
+        // (all loads issued before the first use: one round trip, not nxc)
+        JacPart<T> pr[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (r >= nxc) break;
+          pr[r] = cluster.map_shared_rank(part, (unsigned)r)[(size_t)par * npair + i];
         }
-      }
-    }
-    __syncthreads();
-    if (!s_fail) precond_qr_q(Mat, k, kp, vb0, vb1, hb0, hb1, tau, qv);
-    int done_rounds = 0;
-    unsigned long long t_last = jac_now();
-    while (!s_fail) {
-      if (threadIdx.x == 0) {
-        int tt = jac_ld_acquire(total);
-        int avail = (tt >= 0) ? tt : jac_ld_acquire(progress);
-        unsigned spins = 0;
-        while (avail <= done_rounds && tt < 0) {
-          if ((++spins & 255) == 0 && jac_now() - t_last > 1000000000ull) {
-            s_fail = 1;
-            break;
+        al = be = ga = T(0);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (r >= nxc) break;
+          al += pr[r].al;
+          be += pr[r].be;
+          ga += pr[r].ga;
+        }
+        T cs, sn;
+        jac_rotation(al, be, ga, tol, cs, sn);
+        if (sn != T(0)) {
+          T *sp = S + (size_t)p * hb, *sq = S + (size_t)q * hb;
+#pragma unroll
+          for (int l = 0; l < JAC_NVL; ++l) {
+            if (LPP * l >= nvec) break;
+            const int v = gl + LPP * l;
+            if (v < nvec) {
+              Vec16<T> xo, yo;
+              if constexpr (sizeof(T) == 4) {  // packed pairs (f32x2)
+                const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), n2 = make_float2(-sn, -sn);
+                const float2 xl = make_float2(xr[l].v[0], xr[l].v[1]), xh = make_float2(xr[l].v[2], xr[l].v[3]);
+                const float2 yl = make_float2(yr[l].v[0], yr[l].v[1]), yh = make_float2(yr[l].v[2], yr[l].v[3]);
+                const float2 ol = __ffma2_rn(c2, xl, __fmul2_rn(n2, yl)), oh = __ffma2_rn(c2, xh, __fmul2_rn(n2, yh));
+                const float2 pl = __ffma2_rn(s2, xl, __fmul2_rn(c2, yl)), ph = __ffma2_rn(s2, xh, __fmul2_rn(c2, yh));
+                xo.v[0] = ol.x;
+                xo.v[1] = ol.y;
+                xo.v[2] = oh.x;
+                xo.v[3] = oh.y;
+                yo.v[0] = pl.x;
+                yo.v[1] = pl.y;
+                yo.v[2] = ph.x;
+                yo.v[3] = ph.y;
+              } else {
+#pragma unroll
+                for (int u = 0; u < VN; ++u) {
+                  xo.v[u] = cs * xr[l].v[u] - sn * yr[l].v[u];
+                  yo.v[u] = sn * xr[l].v[u] + cs * yr[l].v[u];
+                }
+              }
+              st16(sp + v * VN, xo);
+              st16(sq + v * VN, yo);
+            }
           }
-          tt = jac_ld_acquire(total);
-          avail = (tt >= 0) ? tt : jac_ld_acquire(progress);
+          nrot += (gl == 0);
         }
-        t_last = jac_now();
-        s_avail = avail;
-        s_tot = tt;
       }
-      __syncthreads();
-      if (s_fail) break;
-      const int avail = s_avail, tot = s_tot;
-      for (int rd = done_rounds; rd < avail; ++rd) {
-        const int t = rd % (kk - 1);
-        for (int i = wid * JAC_PPW + (lane >> 3); i < npair; i += nwarp * JAC_PPW) {
-          const T *e = rlog + ((size_t)rd * npair + i) * 2;
-          const T cs = __ldcg(e), sn = __ldcg(e + 1);  // L2 only: the line may hold later rounds
-          if (sn == T(0)) continue;
-          int p, q;
-          rr_pair(t, i, kk, p, q);
-          rotate_cols(Mat, kp, nv, p, q, cs, sn, g8);
-        }
-        __syncthreads();
-      }
-      done_rounds = avail;
-      if (tot >= 0 && done_rounds >= tot) break;
       __syncthreads();
     }
-    if (threadIdx.x == 0 && s_fail) set_status(ctl, STATUS_TIMEOUT);
+    // block 0's decision, broadcast: every block leaves after the same sweep
+    nrot = warp_sum(nrot);
+    if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
+    __syncthreads();
+    if (rank == 0 && threadIdx.x < C)
+      *cluster.map_shared_rank(&s_done, (unsigned)threadIdx.x) = (s_rot == 0) ? 1 : 0;
+    if (rank == 0 && threadIdx.x == 0 && sweeps < 16) ctl[CTL_SWEEP_ROT0 + sweeps] = s_rot;
+    cluster.sync();
+    done = (s_done != 0);
+    if (threadIdx.x == 0) s_rot = 0;
   }
-  cluster.sync();  // the ranks are now in rank 1's shared memory
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int c = e / k, r = e - c * k;
+  if (rank == 0 && threadIdx.x == 0) ctl[CTL_JACOBI_SWEEPS] = sweeps;
+  // sigma: partial column norms over the X rows, exchanged like the rounds
+  {
+    const int par = round & 1;  // the parity the last round did not use
+    T *pn = reinterpret_cast<T *>(part + (size_t)par * npair);  // [kk]: this block's partial norms
+    if (rank < nxc) {
+      for (int c = wid; c < kk; c += nwarp) {
+        T acc = T(0);
+        for (int v = lane; v < nvx; v += 32) {
+          const Vec16<T> x = ld16(S + (size_t)c * hb + v * VN);
+#pragma unroll
+          for (int u = 0; u < VN; ++u) acc = fma(x.v[u], x.v[u], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) pn[c] = acc;
+      }
+    }
+    cluster.sync();
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) {
+      T s2 = T(0);
+      for (int r = 0; r < nxc; ++r) s2 += cluster.map_shared_rank(pn, (unsigned)r)[c];
+      sig[c] = sqrt(s2);
+    }
+    cluster.sync();  // no block leaves while another may still read its partial norms
+  }
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const T sc = sig[c];
+    int rk = 0;
+    for (int d = 0; d < k; ++d) {
+      const T sd = sig[d];
+      rk += (sd > sc) || (sd == sc && d < c);
+    }
+    rnk[c] = rk;
+    if (rank == 0) Sout[rk] = sc;
+  }
+  __syncthreads();
+  // outputs: U from the rows of X (normalised columns of W), V from the rows of J
+  for (int e = threadIdx.x; e < k * hb; e += blockDim.x) {
+    const int c = e / hb, lr = e - c * hb, gr = r0 + lr;
     const int rk = rnk[c];
-    if (rank == 0) {
-      // the normalised columns of W are the left singular vectors of M
+    if (gr < k) {
       const T sc = sig[c];
-      Uout[(size_t)r * k + rk] = (sc > T(0)) ? Mat[(size_t)c * kp + r] / sc : ((r == rk) ? T(1) : T(0));
-      if (r == 0) Sout[rk] = sc;
-    } else {
-      Vout[(size_t)r * k + rk] = Mat[(size_t)c * kp + r];  // Q J: right singular vectors of M
+      Uout[(size_t)gr * k + rk] = (sc > T(0)) ? S[(size_t)c * hb + lr] / sc : ((gr == rk) ? T(1) : T(0));
+    } else if (gr >= kp && gr - kp < k) {
+      Vout[(size_t)(gr - kp) * k + rk] = S[(size_t)c * hb + lr];
     }
   }
-  cluster.sync();  // neither CTA leaves while the other may still read its shared memory
 }
-
 
 }  // namespace ffq
