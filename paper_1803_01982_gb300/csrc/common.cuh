@@ -23,9 +23,6 @@ enum CtlSlot : int {
   CTL_BARRIER2 = 10,
   CTL_JACOBI_SWEEPS = 11,
   CTL_NONFINITE = 12,
-  CTL_JAC_PROGRESS = 13,  // Jacobi rounds published to the rotation log
-  CTL_JAC_TOTAL = 14,     // Jacobi total rounds (-1 while running)
-  CTL_JAC_QR = 15,        // 1 once the preconditioning reflectors are in global memory
   CTL_SWEEP_ROT0 = 16,  // rotations performed in Jacobi sweeps 0..15 (diagnostic)
   CTL_WORDS = 32,
 };

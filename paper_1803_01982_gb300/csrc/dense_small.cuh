@@ -680,8 +680,6 @@ __global__ void init_ctl_kernel(int *ctl, double *dctl) {
     dctl[D_G2_FIRST] = 1.0;
     ctl[CTL_CAND_FIRST] = -1;
     ctl[CTL_CAND] = 0x7fffffff;
-    ctl[CTL_JAC_PROGRESS] = 0;
-    ctl[CTL_JAC_TOTAL] = -1;
   }
 }
 
