@@ -4,14 +4,16 @@
 //
 //   M^T = Q R (Householder, no pivoting), X = R^T, X J = W diag(sigma):
 //   pairs of columns of X (rows of R) are rotated until every pair is
-//   orthogonal to within tol * ||x_p|| ||x_q||; J, started at Q, accumulates
+//   orthogonal to within tol * ||x_p|| ||x_q||; J, started at I, accumulates
 //   the rotations.  Then M^T = (Q J) diag(sigma) W^T, i.e. U = W normalised
 //   and V = Q J.  The rows of R are graded like the singular values, which
 //   makes the sweeps converge in about a third fewer sweeps than on M^T
 //   itself (the QR preconditioning of one-sided Jacobi of Drmac and Veselic,
 //   without the column pivoting, which gains nothing here).
 //
-// The QR runs in two single-block kernels (R and the reflectors; then Q).
+// The QR runs in two single-block kernels: R and the reflectors first; Q is
+// then formed alongside the sweeps (the caller runs it on a second stream)
+// and V = Q J is one small product afterwards.
 // The sweeps run on a cluster of C blocks (C = 2, 4 or 8).  The rows of the
 // stacked matrix [X; J] (2 kp rows, kk columns) are split into C slabs, one
 // per block, each held column-major in shared memory.  One round of the
@@ -21,21 +23,30 @@
 //      and the per-warp work of a round, few) load their slices of columns p
 //      and q of the slab into registers and form the partial sums of
 //      ||x_p||^2, ||x_q||^2 and x_p . x_q over the X rows of the slab;
-//   2. the partials go to the block's own shared memory (slot [round
-//      parity][pair]);
-//   3. one cluster barrier;
-//   4. every block reads the partials of the blocks holding X rows through
-//      distributed shared memory and adds them in block order, so all blocks
-//      take the same rotation (cos, sin) and the same convergence decisions;
-//      it rotates its registers and stores them back;
+//   2. the blocks holding X rows push their partials with st.async into a
+//      slot [round parity][source block][pair] of every block's shared
+//      memory, completing on that block's mbarrier of the round parity; the
+//      other blocks push one 16-byte token to each X block.  A block sends its
+//      round-r message only after it has read its round r-1 slots, and sends
+//      round r+1 only after receiving every block's round-r message, so no slot
+//      is overwritten before it is read;
+//   3. every block waits (bounded) for its mbarrier phase: nxc * npair
+//      partials, plus the tokens at the X blocks;
+//   4. every block adds the received partials in block order, so all blocks
+//      take bitwise the same rotation (cos, sin) and the same convergence
+//      decisions; it rotates its registers and stores them back;
 //   5. one block barrier (the next round pairs the columns differently).
 // The slab of a block is 1/C of the matrix, so the shared-memory traffic of a
-// round (one read and one write of the slab) and its latency shrink with C.
+// round (one read and one write of the slab) shrinks with C; the exchange
+// costs one one-way DSMEM latency per round, with no cluster barrier.
 // After a sweep without rotations, sigma_c = ||x_c|| (one more exchange of
 // partial norms), the columns are ranked by descending sigma and each block
-// writes its rows of U (from X) and V (from J).  There are no spin-waits: all
-// blocks run the same sequence of barriers, the rounds of a sweep being fixed
-// in number and the end of the sweeps being block 0's decision, broadcast.
+// writes its rows of U (from X) and V (from J).  Every block runs the same
+// sequence of cluster barriers (one per sweep, for block 0's broadcast end
+// decision, and the final ones): the rounds of a sweep are fixed in number.
+// An mbarrier wait that gives up (about a second) marks the block failed: it
+// skips its later waits, block 0 then ends the sweeps, and the run reports
+// STATUS_TIMEOUT.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -412,9 +423,39 @@ __host__ __device__ inline JacGeom jac_geom(int k, int C, int VN) {
 }
 inline size_t jac_cluster_smem(int k, int C, size_t elem) {
   const JacGeom g = jac_geom(k, C, 16 / (int)elem);
-  return (size_t)g.kk * g.hb * elem + 2 * (size_t)g.npair * sizeof(JacPart<double>) +
-         (size_t)g.kk * elem + (size_t)g.kk * sizeof(int) + 64;
+  const size_t slab = ((size_t)g.kk * g.hb * elem + 15) & ~(size_t)15;
+  return slab + 2 * (size_t)C * g.npair * 4 * elem + (size_t)g.kk * elem + (size_t)g.kk * sizeof(int) + 64;
 }
+
+// Shared-memory address helpers for the asynchronous exchange.
+__device__ __forceinline__ unsigned jac_saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned jac_mapa(unsigned a, int r) {
+  unsigned d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(r));
+  return d;
+}
+// 16 bytes to another block's shared memory, completing on its mbarrier.
+__device__ __forceinline__ void jac_st_async(unsigned raddr, unsigned rmbar, float a, float b, float c, float d) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   raddr),
+               "f"(a), "f"(b), "f"(c), "f"(d), "r"(rmbar)
+               : "memory");
+}
+__device__ __forceinline__ void jac_st_async(unsigned raddr, unsigned rmbar, double a, double b) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "d"(a), "d"(b), "r"(rmbar)
+               : "memory");
+}
+__device__ __forceinline__ bool jac_try_wait(unsigned mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr long long JAC_WAIT_SPINS = 1ll << 22;  // bounded mbarrier wait (about a second)
 
 // Xin: X (column-major, X(r, c) at Xin[c * k + r]); Jin: J_0 (same layout) or
 // NULL for the identity.  Uout, Vout: k x k row-major, columns in descending
@@ -436,11 +477,12 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
   const int nvx = max(0, min(nvec, (kp - r0) / VN));      // of which rows of X
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);                           // column c at S[c * hb]
-  JacPart<T> *part = reinterpret_cast<JacPart<T> *>(
-      smem_raw + (((size_t)kk * hb * sizeof(T) + 15) & ~(size_t)15));  // [2][npair]: this block's partials
-  T *sig = reinterpret_cast<T *>(part + 2 * (size_t)npair);         // [kk]
+  JacPart<T> *inbox = reinterpret_cast<JacPart<T> *>(
+      smem_raw + (((size_t)kk * hb * sizeof(T) + 15) & ~(size_t)15));  // [2][C][npair]: partials received
+  T *sig = reinterpret_cast<T *>(inbox + 2 * (size_t)C * npair);    // [kk]
   int *rnk = reinterpret_cast<int *>(sig + kk);                     // [kk]
-  __shared__ int s_rot, s_done;
+  __shared__ __align__(8) unsigned long long s_mbar[2];             // one per round parity
+  __shared__ int s_rot, s_done, s_fail;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int gl = lane % LPP;  // lane within the pair's group
   if (max_sweeps > JAC_MAX_SWEEPS) max_sweeps = JAC_MAX_SWEEPS;
@@ -459,10 +501,19 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
     }
     S[e] = v;
   }
-  if (threadIdx.x == 0) s_rot = 0;
+  if (threadIdx.x == 0) {
+    s_rot = 0;
+    s_fail = 0;
+    for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(jac_saddr(&s_mbar[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   if (rank == 0 && threadIdx.x < 16) ctl[CTL_SWEEP_ROT0 + threadIdx.x] = 0;
   __syncthreads();
-  cluster.sync();  // every block has started before any block reads another's shared memory
+  cluster.sync();  // every block's barriers exist before any block sends to them
+  // bytes a block receives per round: the partials of every X block, and at
+  // the X blocks one 16-byte token from every other block ("your slot of the
+  // round before last is free again")
+  const unsigned expect = (unsigned)(nxc * npair * sizeof(JacPart<T>) + (rank < nxc ? (C - nxc) * 16 : 0));
 
   const int i = threadIdx.x / LPP;
   int round = 0, sweeps = 0;
@@ -515,25 +566,44 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
         ga += __shfl_xor_sync(0xffffffffu, ga, o);
       }
       const int par = round & 1;
-      if (p >= 0 && rank < nxc && gl == 0) part[(size_t)par * npair + i] = JacPart<T>{al, be, ga, T(0)};
-      cluster.sync();
+      JacPart<T> *in = inbox + (size_t)par * C * npair;  // [C][npair]
+      const unsigned mbar = jac_saddr(&s_mbar[par]);
+      if (rank < nxc) {
+        // this block's partials to every block (the group's lanes share the destinations)
+        if (p >= 0)
+          for (int d = gl; d < C; d += LPP) {
+            const unsigned ra = jac_mapa(jac_saddr(in + (size_t)rank * npair + i), d), rm = jac_mapa(mbar, d);
+            if constexpr (sizeof(T) == 4) {
+              jac_st_async(ra, rm, (float)al, (float)be, (float)ga, 0.f);
+            } else {
+              jac_st_async(ra, rm, (double)al, (double)be);
+              jac_st_async(ra + 16, rm, (double)ga, 0.0);
+            }
+          }
+      } else if (threadIdx.x < nxc) {
+        const int d = threadIdx.x;
+        jac_st_async(jac_mapa(jac_saddr(in + (size_t)rank * npair), d), jac_mapa(mbar, d), 0.f, 0.f, 0.f, 0.f);
+      }
+      if (threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(expect) : "memory");
+      if (!s_fail) {
+        const unsigned phase = (unsigned)((round >> 1) & 1);
+        long long spins = 0;
+        while (!jac_try_wait(mbar, phase))
+          if (++spins > JAC_WAIT_SPINS) {
+            s_fail = 1;  // sticky: later rounds skip the wait; the sweeps end at block 0's next decision
+            break;
+          }
+      }
       if (p >= 0) {
         // the partials of the blocks holding X rows, added in block order:
         // the same sums, hence the same rotations, in every block
-        // (all loads issued before the first use: one round trip, not nxc)
-        JacPart<T> pr[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          if (r >= nxc) break;
-          pr[r] = cluster.map_shared_rank(part, (unsigned)r)[(size_t)par * npair + i];
-        }
         al = be = ga = T(0);
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          if (r >= nxc) break;
-          al += pr[r].al;
-          be += pr[r].be;
-          ga += pr[r].ga;
+        for (int r = 0; r < nxc; ++r) {
+          const JacPart<T> pr = in[(size_t)r * npair + i];
+          al += pr.al;
+          be += pr.be;
+          ga += pr.ga;
         }
         T cs, sn;
         jac_rotation(al, be, ga, tol, cs, sn);
@@ -580,17 +650,19 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
     if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
     if (rank == 0 && threadIdx.x < C)
-      *cluster.map_shared_rank(&s_done, (unsigned)threadIdx.x) = (s_rot == 0) ? 1 : 0;
+      *cluster.map_shared_rank(&s_done, (unsigned)threadIdx.x) = (s_rot == 0 || s_fail) ? 1 : 0;
     if (rank == 0 && threadIdx.x == 0 && sweeps < 16) ctl[CTL_SWEEP_ROT0 + sweeps] = s_rot;
     cluster.sync();
     done = (s_done != 0);
     if (threadIdx.x == 0) s_rot = 0;
   }
   if (rank == 0 && threadIdx.x == 0) ctl[CTL_JACOBI_SWEEPS] = sweeps;
-  // sigma: partial column norms over the X rows, exchanged like the rounds
+  if (threadIdx.x == 0 && s_fail) set_status(ctl, STATUS_TIMEOUT);
+  // sigma: partial column norms over the X rows, pulled through DSMEM after a
+  // cluster barrier (the inbox of the parity the last round did not use is free)
   {
-    const int par = round & 1;  // the parity the last round did not use
-    T *pn = reinterpret_cast<T *>(part + (size_t)par * npair);  // [kk]: this block's partial norms
+    const int par = round & 1;
+    T *pn = reinterpret_cast<T *>(inbox + (size_t)par * C * npair);  // [kk]: this block's partial norms
     if (rank < nxc) {
       for (int c = wid; c < kk; c += nwarp) {
         T acc = T(0);
