@@ -42,15 +42,123 @@ struct QrcpArgs {
   int s_pad;           // slab column stride in shared memory
 };
 
+// 16-byte vector of T in shared memory.
+template <typename T>
+struct QVec {
+  static constexpr int N = 16 / sizeof(T);
+  T v[N];
+};
+template <typename T>
+__device__ __forceinline__ QVec<T> qld(const T *p) {
+  QVec<T> r;
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    r.v[0] = x.x;
+    r.v[1] = x.y;
+    r.v[2] = x.z;
+    r.v[3] = x.w;
+  } else {
+    const double2 x = *reinterpret_cast<const double2 *>(p);
+    r.v[0] = x.x;
+    r.v[1] = x.y;
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void qst(T *p, const QVec<T> &r) {
+  if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  else *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
+}
+
+// NC columns x_u = col0 + u * ld := (I - tau v v^T) x_u on 16-byte vectors
+// q0 .. nq - 1, and their trailing squared norms over rows > j; one warp.
+// v is zero above row j, so rows above j are left as they are.
+template <typename T, int NC>
+__device__ __forceinline__ void apply_reflector_group(T *col0, int ld, const T *v, T tau, int j, int q0, int nq,
+                                                      T *nrm_out) {
+  constexpr int VN = QVec<T>::N;
+  const int lane = threadIdx.x & 31;
+  T w[NC], acc[NC];
+#pragma unroll
+  for (int u = 0; u < NC; ++u) w[u] = T(0);
+  for (int q = q0 + lane; q < nq; q += 32) {
+    const QVec<T> vv = qld(v + q * VN);
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const QVec<T> xx = qld(col0 + (size_t)u * ld + q * VN);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) w[u] = fma(vv.v[e], xx.v[e], w[u]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int u = 0; u < NC; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+  }
+#pragma unroll
+  for (int u = 0; u < NC; ++u) {
+    w[u] *= tau;
+    acc[u] = T(0);
+  }
+  for (int q = q0 + lane; q < nq; q += 32) {
+    const QVec<T> vv = qld(v + q * VN);
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      T *px = col0 + (size_t)u * ld + q * VN;
+      QVec<T> xx = qld(px);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) {
+        const T y = fma(-w[u], vv.v[e], xx.v[e]);
+        xx.v[e] = y;
+        if (q * VN + e > j) acc[u] = fma(y, y, acc[u]);
+      }
+      qst(px, xx);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int u = 0; u < NC; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int u = 0; u < NC; ++u)
+      if (nrm_out[u] >= T(0)) nrm_out[u] = acc[u];  // selected columns keep their mark
+  }
+}
+
+// Step 4 over the block's ncol columns: contiguous runs per warp, in groups of
+// 8, 4, 2, 1 so that each warp keeps several independent reductions in flight.
+// Selected columns are transformed too (their values are not used again).
+template <typename T>
+__device__ __forceinline__ void apply_reflector_cols(T *slab, int ld, int ncol, const T *v, T tau, int j, T *nrm) {
+  constexpr int VN = QVec<T>::N;
+  const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int q0 = j / VN, nq = ld / VN;
+  const int per = (ncol + nwarp - 1) / nwarp;
+  int c = wid * per;
+  const int ce = min(ncol, c + per);
+  for (; c + 8 <= ce; c += 8) apply_reflector_group<T, 8>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
+  if (c + 4 <= ce) {
+    apply_reflector_group<T, 4>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
+    c += 4;
+  }
+  if (c + 2 <= ce) {
+    apply_reflector_group<T, 2>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
+    c += 2;
+  }
+  if (c < ce) apply_reflector_group<T, 1>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *slab = reinterpret_cast<T *>(smem_raw);                        // [cols][s_pad]
-  T *nrm = slab + (size_t)a.cols_per_block * a.s_pad;               // [cols]
-  T *v = nrm + a.cols_per_block;                                    // [s_pad]
+  T *slab = reinterpret_cast<T *>(smem_raw);                        // [cols][s_pad], rows >= s zero
+  T *v = slab + (size_t)a.cols_per_block * a.s_pad;                 // [s_pad] (16-byte aligned)
+  T *nrm = v + a.s_pad;                                             // [cols]
   __shared__ T red_v[32];
   __shared__ int red_i[32];
-  __shared__ T s_tau, s_beta;
+  __shared__ T s_tau, s_beta, s_scal;
   __shared__ int s_win_blk, s_win_col;
 
   const int G = gridDim.x, b = blockIdx.x;
@@ -60,11 +168,11 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   unsigned *bar = reinterpret_cast<unsigned *>(a.ctl + CTL_BARRIER0);
 
-  // load slab, initial norms
+  // load slab (zero padding rows), initial norms
   for (int c = wid; c < ncol; c += nwarp) {
     T acc = T(0);
-    for (int t = lane; t < s; t += 32) {
-      const T x = a.Bt[(c0 + c) * a.lds + t];
+    for (int t = lane; t < a.s_pad; t += 32) {
+      const T x = (t < s) ? a.Bt[(c0 + c) * a.lds + t] : T(0);
       slab[(size_t)c * a.s_pad + t] = x;
       acc += x * x;
     }
@@ -148,6 +256,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
         }
         s_tau = tau;
         s_beta = beta;
+        s_scal = (tau != T(0)) ? T(1) / (alpha - beta) : T(0);
         if (b == 0) a.piv[j] = wi;
         a.sel[wi] = 1;
       }
@@ -158,41 +267,19 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
         for (int t = threadIdx.x; t < a.k; t += blockDim.x)
           a.S11[(size_t)t * a.k + j] = (t < j) ? v[t] : ((t == j) ? beta : T(0));
       }
-      if (tau != T(0)) {
-        const T scal = T(1) / (v[j] - beta);
-        for (int t = j + 1 + threadIdx.x; t < s; t += blockDim.x) v[t] *= scal;
-      }
       __syncthreads();
-      if (threadIdx.x == 0) v[j] = T(1);
+      {
+        // v as the full-length reflector: zeros above row j and in the
+        // padding, 1 at row j; rows above j then see v = 0 and stay as they are
+        const T scal = s_scal;
+        for (int t = threadIdx.x; t < a.s_pad; t += blockDim.x)
+          v[t] = (t < j || t >= s) ? T(0) : ((t == j) ? T(1) : v[t] * scal);
+      }
       if (b == wb && threadIdx.x == 0) nrm[wi - c0] = T(-1);  // selected
       __syncthreads();
-      // 4. apply H to own unselected columns, recompute trailing norms
-      if (tau != T(0)) {
-        for (int c = wid; c < ncol; c += nwarp) {
-          if (nrm[c] < T(0)) continue;
-          T *col = slab + (size_t)c * a.s_pad;
-          T w = T(0);
-          for (int t = j + lane; t < s; t += 32) w += v[t] * col[t];
-          w = warp_sum(w) * tau;
-          T acc = T(0);
-          for (int t = j + lane; t < s; t += 32) {
-            const T y = col[t] - w * v[t];
-            col[t] = y;
-            if (t > j) acc += y * y;
-          }
-          acc = warp_sum(acc);
-          if (lane == 0) nrm[c] = acc;
-        }
-      } else {
-        for (int c = wid; c < ncol; c += nwarp) {
-          if (nrm[c] < T(0)) continue;
-          const T *col = slab + (size_t)c * a.s_pad;
-          T acc = T(0);
-          for (int t = j + 1 + lane; t < s; t += 32) acc += col[t] * col[t];
-          acc = warp_sum(acc);
-          if (lane == 0) nrm[c] = acc;
-        }
-      }
+      // 4. apply H to the block's columns and recompute the unselected ones'
+      //    trailing norms ||B(j+1:s, i)||^2 (tau = 0: norms only)
+      apply_reflector_cols(slab, a.s_pad, ncol, v, tau, j, nrm);
       __syncthreads();
     }
   }
