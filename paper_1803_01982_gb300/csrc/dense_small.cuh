@@ -175,6 +175,93 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
   }
 }
 
+// Single precision, 2*RP rows per warp held as row pairs, so each update is
+// one packed f32x2 FMA for two rows (same arithmetic as trsm_rows_kernel).
+template <int NS, int RP, bool FWD>
+__global__ void __launch_bounds__(512) trsm_rows2_kernel(float *__restrict__ X, int64_t ldx, int64_t M, int k,
+                                                         const float *__restrict__ Pm, int64_t psi, int64_t psj,
+                                                         const int *gate) {
+  if (gate && *gate == 0) return;  // gated recomputation (see extract_r11_kernel)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *Ps = reinterpret_cast<float *>(smem_raw);  // k x k, row-major, P(j, c) at Ps[j*k + c]
+  float *dinv = Ps + (size_t)k * k;                 // 1 / P(j, j)
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    Ps[e] = Pm[(int64_t)i * psi + (int64_t)j * psj];
+  }
+  for (int j = threadIdx.x; j < k; j += blockDim.x) dinv[j] = 1.f / Pm[(int64_t)j * psi + (int64_t)j * psj];
+  __syncthreads();
+  constexpr int R = 2 * RP;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t ngroups = (M + R - 1) / R;
+  for (int64_t grp = (int64_t)blockIdx.x * nwarp + wid; grp < ngroups; grp += (int64_t)gridDim.x * nwarp) {
+    const int64_t r0 = grp * R;
+    float2 x[RP][NS];  // x[rp][sl] = rows (r0 + 2 rp, r0 + 2 rp + 1), column lane + 32 sl
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int c = lane + 32 * sl;
+        const int64_t ra = r0 + 2 * rp, rb = ra + 1;
+        x[rp][sl].x = (ra < M && c < k) ? X[ra * ldx + c] : 0.f;
+        x[rp][sl].y = (rb < M && c < k) ? X[rb * ldx + c] : 0.f;
+      }
+    auto step = [&](int j, int jb, int ln, int slo, int shi) {
+      const float di = dinv[j];
+      float2 y[RP];
+#pragma unroll
+      for (int rp = 0; rp < RP; ++rp) {
+        y[rp].x = __shfl_sync(0xffffffffu, x[rp][jb].x * di, ln);
+        y[rp].y = __shfl_sync(0xffffffffu, x[rp][jb].y * di, ln);
+      }
+      if (lane == ln) {
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp) x[rp][jb] = y[rp];
+      }
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        if (sl < slo || sl > shi) continue;
+        const int c = lane + 32 * sl;
+        const bool on = FWD ? (c > j && c < k) : (c < j);
+        const float pc = on ? Ps[j * k + c] : 0.f;
+        const float2 p2 = make_float2(pc, pc);
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp) x[rp][sl] = __ffma2_rn(make_float2(-y[rp].x, -y[rp].y), p2, x[rp][sl]);
+      }
+    };
+    if (FWD) {
+#pragma unroll
+      for (int jb = 0; jb < NS; ++jb) {
+#pragma unroll 1
+        for (int ln = 0; ln < 32; ++ln) {
+          const int j = jb * 32 + ln;
+          if (j >= k) break;
+          step(j, jb, ln, jb, NS - 1);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int jb = NS - 1; jb >= 0; --jb) {
+#pragma unroll 1
+        for (int ln = 31; ln >= 0; --ln) {
+          const int j = jb * 32 + ln;
+          if (j >= k) continue;
+          step(j, jb, ln, 0, jb);
+        }
+      }
+    }
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int c = lane + 32 * sl;
+        const int64_t ra = r0 + 2 * rp, rb = ra + 1;
+        if (ra < M && c < k) X[ra * ldx + c] = x[rp][sl].x;
+        if (rb < M && c < k) X[rb * ldx + c] = x[rp][sl].y;
+      }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky  W = R^T R  (one block; W symmetric k x k, only its upper triangle
 // is read).  R is written upper triangular (k x k, zero below).  A non-positive

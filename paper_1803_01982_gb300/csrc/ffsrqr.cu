@@ -302,19 +302,30 @@ int launch_trsm(cudaStream_t st, const ffsrqr_plan_s *P, T *X, int64_t ldx, int6
   const int threads = 512;
   // rows per warp: many rows -> 8 (FP32) / 4 (FP64) for reuse of each pivot
   // row; few rows (a k x k inverse) -> 1, to spread them over more warps
+  // FP32 many rows: 10 rows per warp as 5 packed row pairs, so that one wave of
+  // warps (num_sms x 16) covers 20000 rows without a second round
   const bool few = M < 4096;
-  const int rr = few ? 1 : ((sizeof(T) == 4) ? 8 : 4);
+  const bool packed = !few && sizeof(T) == 4;
+  const int rr = few ? 1 : (packed ? 10 : 4);
   const int64_t groups = cdiv(M, rr);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(groups, threads / 32), P->num_sms));
   const int ns = (int)cdiv(k, 32);
-#define TRSM_CASE(NSv)                                                                        \
-  if (ns <= NSv) {                                                                            \
-    auto fn = few ? trsm_rows_kernel<T, NSv, 1, FWD>                                          \
-                  : trsm_rows_kernel<T, NSv, (sizeof(T) == 4) ? 8 : 4, FWD>;                  \
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-    fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj, gate);                        \
-    CKL("trsm_rows");                                                                         \
-    return 0;                                                                                 \
+#define TRSM_CASE(NSv)                                                                                 \
+  if (ns <= NSv) {                                                                                     \
+    if constexpr (sizeof(T) == 4) {                                                                    \
+      if (packed) {                                                                                    \
+        auto fn2 = trsm_rows2_kernel<NSv, 5, FWD>;                                                     \
+        CK(cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
+        fn2<<<grid, threads, smem, st>>>((float *)X, ldx, M, k, (const float *)Pm, psi, psj, gate);    \
+        CKL("trsm_rows2");                                                                             \
+        return 0;                                                                                      \
+      }                                                                                                \
+    }                                                                                                  \
+    auto fn = few ? trsm_rows_kernel<T, NSv, 1, FWD> : trsm_rows_kernel<T, NSv, 4, FWD>;               \
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));              \
+    fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj, gate);                                 \
+    CKL("trsm_rows");                                                                                  \
+    return 0;                                                                                          \
   }
   TRSM_CASE(1)
   TRSM_CASE(2)
