@@ -261,6 +261,11 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   sc.vec4 = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0);
   // few tiles shared by many blocks (a Gram): one row per fixup block
   sc.fix_rows = (8LL * sc.tiles < sc.G) ? 1 : 4;
+  // short K (a tall matrix times a k x k factor): whole tiles per block,
+  // written directly, no fixup; the extra tile some blocks take costs less
+  // than the partials and their fixup
+  sc.whole_tiles = (sc.KB <= 64) ? 1 : 0;
+  if (sc.whole_tiles) sc.G = std::min(sc.G, sc.tiles);
   int stage_bytes = 0;
   if (nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true>::bytes(ntile);
   else if (nprod == 3 && a_mn) stage_bytes = TcStage<16, 3, true>::bytes(ntile);
@@ -283,8 +288,10 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   else return FFSRQR_STATUS_UNSUPPORTED;
 #undef TC_LAUNCH
   CKL("tc_gemm");
-  tc_fixup_kernel<<<dim3(sc.tiles, TC_BM / sc.fix_rows), 256, 0, st>>>(sc);
-  CKL("tc_fixup");
+  if (!sc.whole_tiles) {
+    tc_fixup_kernel<<<dim3(sc.tiles, TC_BM / sc.fix_rows), 256, 0, st>>>(sc);
+    CKL("tc_fixup");
+  }
   return 0;
 }
 

@@ -44,7 +44,9 @@
 // block's first and last segments may cover part of a tile's K range; those
 // partial tiles go to part[(2c + slot)] and tc_fixup_kernel adds the pieces of
 // each tile in block order (deterministic).  All other tiles are written
-// directly.  Every mbarrier wait is bounded (~1 s); on expiry the block
+// directly.  With a short K (sc.whole_tiles) block c owns the whole tiles
+// [tiles*c/G, tiles*(c+1)/G) instead: every tile is written directly and no
+// fixup runs.  Every mbarrier wait is bounded (~1 s); on expiry the block
 // records STATUS_TIMEOUT, drains what it issued, frees its TMEM and exits.
 #pragma once
 
@@ -78,6 +80,7 @@ struct TcSched {
   int *ctl;
   int vec4;         // C rows are 16-byte aligned (C % 16 == 0, ldc % 4 == 0)
   int fix_rows;     // rows of a tile per fixup block (divides TC_BM)
+  int whole_tiles;  // 1: block c takes tiles [tiles c / G, tiles (c+1) / G) whole (no partials)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -284,8 +287,13 @@ __global__ void __maxnreg__(168)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x;
   SegIter it;
-  it.u = (sc.U * c) / sc.G;
-  it.u1 = (sc.U * (c + 1)) / sc.G;
+  if (sc.whole_tiles) {
+    it.u = (long long)(((long long)sc.tiles * c) / sc.G) * sc.KB;
+    it.u1 = (long long)(((long long)sc.tiles * (c + 1)) / sc.G) * sc.KB;
+  } else {
+    it.u = (sc.U * c) / sc.G;
+    it.u1 = (sc.U * (c + 1)) / sc.G;
+  }
   it.KB = sc.KB;
   const int first_tile = (int)(it.u / sc.KB);
 
