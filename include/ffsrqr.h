@@ -94,7 +94,9 @@ typedef struct {
  * The plan holds only host metadata; it is bound to the current CUDA device.
  * Errors: -1 plan NULL, -2 m, -3 n, -4 k, -5 p, -6 mode, -7 opts, -8
  * workspace_bytes NULL; FFSRQR_STATUS_UNSUPPORTED for sizes this build does
- * not handle; FFSRQR_STATUS_CUDA if the device query fails. */
+ * not handle (the k x k factors live in one block's shared memory: k <= 224
+ * in FP32 and the mixed mode, k <= 160 in FP64); FFSRQR_STATUS_CUDA if the
+ * device query fails. */
 int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
                 const ffsrqr_opts_t *opts, size_t *workspace_bytes);
 

@@ -988,7 +988,7 @@ int plan_jacobi(ffsrqr_plan_s *P) {
   }
   P->jac_cluster = 0;
   P->jac_lpp = 0;
-  const int cand[7][2] = {{8, 4}, {4, 4}, {8, 2}, {2, 4}, {2, 8}, {4, 8}, {8, 8}};
+  const int cand[7][2] = {{8, 2}, {8, 4}, {4, 4}, {2, 4}, {2, 8}, {4, 8}, {8, 8}};
   for (int ci = 0; ci < 7 && !P->jac_cluster; ++ci) {
     const int C = cand[ci][0], lpp = cand[ci][1];
     const JacGeom g = jac_geom(k, C, vn);
@@ -1061,7 +1061,9 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
   if (opts && opts->max_swaps < 0) return -7;
   if (!workspace_bytes) return -8;
   const int elem = (mode == FFSRQR_FP64) ? 8 : 4;
-  if ((size_t)k * k * elem > 200 * 1024) return FFSRQR_STATUS_UNSUPPORTED;
+  // the k x k factors live in one block's shared memory, and the row solves
+  // hold at most 7 x 32 columns per lane group
+  if ((size_t)k * k * elem > 200 * 1024 || k > 224) return FFSRQR_STATUS_UNSUPPORTED;
   ffsrqr_plan_s *P = new (std::nothrow) ffsrqr_plan_s();
   if (!P) return FFSRQR_STATUS_WORKSPACE;
   P->m = m;

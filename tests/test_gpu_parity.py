@@ -185,3 +185,48 @@ def test_deterministic():
     _, b = run_gpu(A, 30, 10)
     for key in ["U", "S", "V", "piv"]:
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_plain_fp32_largest_k():
+    """k = 224, the largest rank the FP32 plan accepts (7 x 32 columns per row
+    solve; k^2 * 4 bytes <= 200 KiB of shared memory): the small SVD's QR and
+    cluster Jacobi at their limits.  k = 225 is refused at plan time."""
+    with pytest.raises(ffsrqr.FfsrqrError):
+        ffsrqr.Plan(1400, 1100, 225, 10, ffsrqr.PLAIN_FP32)
+    m, n, k, p = 1400, 1100, 224, 10
+    A = synth.decayed(m, n, 0.985 ** np.arange(min(m, n)), 1e-4, seed=21)
+    _, got = run_gpu(A, k, p)
+    ref = oracle.ffsrqr(A, k, p, seed=0)
+    assert got["info"]["status"] == ref.status == 0
+    # past the first near-tie the FP32 pivots may differ from the FP64 oracle's:
+    # properties any good rank-k factorisation has
+    S, So = got["S"], ref.S
+    head = So >= 0.1 * So[0]
+    assert np.all(np.abs(S - So)[head] <= 1e-3 * So[head])
+    A64 = A.astype(np.float64)
+    res = np.linalg.norm(A64 - (got["U"] * S) @ got["V"].T)
+    assert res <= 1.01 * oracle.residual_fro(A64, ref.U, ref.S, ref.V)
+    # V = V' Q J: the FP32 Householder Q of the small SVD's preconditioning and
+    # the accumulated rotations each lose O(k u) orthogonality (measured 7.6e-5
+    # here, 6.6e-5 at k = 200): the bound is 8 k u
+    tol_v = max(2e-5, 8 * k * U32)
+    eu = np.max(np.abs(got["U"].T @ got["U"] - np.eye(k)))
+    ev = np.max(np.abs(got["V"].T @ got["V"] - np.eye(k)))
+    assert eu <= 2e-5, eu
+    assert ev <= tol_v, (ev, tol_v)
+    assert np.allclose(A64 @ got["V"], got["U"] * S, atol=2e-5 * S[0])
+
+
+def test_fp64_largest_k():
+    """k = 160, the largest rank the FP64 plan accepts (k^2 * 8 bytes <= 200 KiB)."""
+    m, n, k, p = 900, 700, 160, 8
+    A = synth.decayed(m, n, 0.98 ** np.arange(min(m, n)), 1e-6, seed=22).astype(np.float64)
+    _, got = run_gpu(A, k, p, ffsrqr.FP64)
+    ref = oracle.ffsrqr(A, k, p, seed=0)
+    assert got["info"]["status"] == ref.status == 0
+    assert list(got["piv"][:k]) == list(ref.piv[:k])
+    np.testing.assert_allclose(got["S"], ref.S, rtol=1e-10)
+    res = np.linalg.norm(A - (got["U"] * got["S"]) @ got["V"].T)
+    assert res == pytest.approx(oracle.residual_fro(A, ref.U, ref.S, ref.V), rel=1e-10)
+    np.testing.assert_allclose(got["U"].T @ got["U"], np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(got["V"].T @ got["V"], np.eye(k), atol=1e-12)
