@@ -258,6 +258,54 @@ int ffsrqr_batch_workspace_offset(ffsrqr_batch_t batch, int32_t i, size_t *offse
 int ffsrqr_batch_destroy(ffsrqr_batch_t batch);
 
 /* ------------------------------------------------------------------------ */
+/* Host-buffer pipeline                                                      */
+/* ------------------------------------------------------------------------ */
+/* Not a step of the paper's algorithm: problems of one plan's shape whose A
+ * and outputs live in host memory.  The copy of problem i+1's A to the device
+ * overlaps the computation of problem i, and problem i's outputs return while
+ * problem i+1 computes (two device buffer sets, one stream per direction). */
+typedef struct ffsrqr_pipe_s *ffsrqr_pipe_t;
+
+/* One problem in host memory (pinned memory lets the copies overlap): A
+ * (m x n, row-major, lda >= n), outputs U (m x k, ldu >= k), S (k), V (n x k,
+ * ldv >= k), piv (int32[n]), as in ffsrqr_run. */
+typedef struct {
+  const void *A;
+  int64_t lda;
+  uint64_t seed;
+  void *U;
+  int64_t ldu;
+  void *S;
+  void *V;
+  int64_t ldv;
+  int32_t *piv;
+} ffsrqr_host_problem_t;
+
+/* Creates a pipeline for plan (which it does not own) and writes the device
+ * memory it needs beside the plan's workspace: two inputs and two output sets
+ * (256-byte aligned).  Returns 0, -1 NULL pipe, -2 NULL plan, -3 NULL
+ * device_bytes, FFSRQR_STATUS_CUDA if its streams or events cannot be made. */
+int ffsrqr_pipe_create(ffsrqr_pipe_t *pipe, ffsrqr_plan_t plan, size_t *device_bytes);
+
+/* Enqueues count problems: for each, host A -> device buffer (H2D stream),
+ * ffsrqr_run on stream, outputs -> host (D2H stream).  device_mem: device,
+ * the size ffsrqr_pipe_create reported, 256-byte aligned; workspace: the
+ * plan's.  stream (NULL = legacy stream) waits for the last output copy, so a
+ * synchronisation of stream makes every output valid.  infos: pinned host
+ * array of count reports, or NULL.  Returns 0, -1 NULL pipe, -2 NULL probs or
+ * a problem with a NULL buffer or a leading dimension below n (A) or k,
+ * -3 device_mem, -4 count < 0, the ffsrqr_run code of a failing problem, or
+ * FFSRQR_STATUS_CUDA. */
+int ffsrqr_pipe_run(ffsrqr_pipe_t pipe, const ffsrqr_host_problem_t *probs, int32_t count, void *device_mem,
+                    void *workspace, void *stream, ffsrqr_info_t *infos);
+
+int ffsrqr_pipe_destroy(ffsrqr_pipe_t pipe);
+
+/* Shape of a plan: m, n, k, p, mode (any pointer may be NULL).  Returns 0, or
+ * -1 for a NULL plan. */
+int ffsrqr_plan_shape(ffsrqr_plan_t plan, int64_t *m, int64_t *n, int32_t *k, int32_t *p, int32_t *mode);
+
+/* ------------------------------------------------------------------------ */
 /* Request server (admission under a memory budget, continuous batching)    */
 /* ------------------------------------------------------------------------ */
 /* Not a step of the paper's algorithm: a serving loop for streams of

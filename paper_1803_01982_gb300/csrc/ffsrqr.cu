@@ -1149,6 +1149,16 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   return rc;
 }
 
+int ffsrqr_plan_shape(ffsrqr_plan_t plan, int64_t *m, int64_t *n, int32_t *k, int32_t *p, int32_t *mode) {
+  if (!plan) return -1;
+  if (m) *m = plan->m;
+  if (n) *n = plan->n;
+  if (k) *k = plan->k;
+  if (p) *p = plan->p;
+  if (mode) *mode = plan->mode;
+  return 0;
+}
+
 int ffsrqr_destroy(ffsrqr_plan_t plan) {
   if (!plan) return -1;
   if (plan->side) {

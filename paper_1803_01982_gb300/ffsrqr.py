@@ -56,6 +56,13 @@ class Request(ctypes.Structure):
                 ("ldv", ctypes.c_int64), ("piv", ctypes.c_void_p)]
 
 
+class HostProblem(ctypes.Structure):
+    """ffsrqr_host_problem_t: one problem of a pipe (host pointers)."""
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64), ("S", ctypes.c_void_p),
+                ("V", ctypes.c_void_p), ("ldv", ctypes.c_int64), ("piv", ctypes.c_void_p)]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -114,6 +121,15 @@ def _load():
     lib.ffsrqr_server_stats.restype = ctypes.c_int
     lib.ffsrqr_server_destroy.argtypes = [P]
     lib.ffsrqr_server_destroy.restype = ctypes.c_int
+    lib.ffsrqr_pipe_create.argtypes = [ctypes.POINTER(P), P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_pipe_create.restype = ctypes.c_int
+    lib.ffsrqr_pipe_run.argtypes = [P, ctypes.POINTER(HostProblem), i32, P, P, P, ctypes.POINTER(Info)]
+    lib.ffsrqr_pipe_run.restype = ctypes.c_int
+    lib.ffsrqr_pipe_destroy.argtypes = [P]
+    lib.ffsrqr_pipe_destroy.restype = ctypes.c_int
+    lib.ffsrqr_plan_shape.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.ffsrqr_plan_shape.restype = ctypes.c_int
     return lib
 
 
@@ -143,6 +159,10 @@ ffsrqr_server_wait = lib.ffsrqr_server_wait
 ffsrqr_server_stats = lib.ffsrqr_server_stats
 ffsrqr_server_destroy = lib.ffsrqr_server_destroy
 ffsrqr_qrcp_static = lib.ffsrqr_qrcp_static
+ffsrqr_pipe_create = lib.ffsrqr_pipe_create
+ffsrqr_pipe_run = lib.ffsrqr_pipe_run
+ffsrqr_pipe_destroy = lib.ffsrqr_pipe_destroy
+ffsrqr_plan_shape = lib.ffsrqr_plan_shape
 
 
 class FfsrqrError(RuntimeError):
@@ -247,6 +267,53 @@ def phase_times(plan: "Plan", back: int = 0) -> dict:
     if cnt < 0:
         raise FfsrqrError(f"ffsrqr_phase_times_back returned {cnt}")
     return {PHASES[i]: buf[i] for i in range(cnt)}
+
+
+class Pipe:
+    """Host-buffer pipeline over one plan (ffsrqr_pipe_*): each problem's A is
+    copied from host memory while the previous problem computes, and the
+    outputs come back to host memory."""
+
+    def __init__(self, plan: "Plan"):
+        import torch
+        self.plan = plan
+        self._h = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        _check(lib.ffsrqr_pipe_create(ctypes.byref(self._h), plan._h, ctypes.byref(nb)), "ffsrqr_pipe_create")
+        self.device_mem = torch.empty(nb.value + 256, dtype=torch.uint8, device=plan.device)
+        self._off = (-self.device_mem.data_ptr()) % 256
+
+    def host_outputs(self):
+        """Pinned host U, S, V, piv for one problem."""
+        import torch
+        p = self.plan
+        return (torch.empty(p.m, p.k, dtype=p.dtype).pin_memory(), torch.empty(p.k, dtype=p.dtype).pin_memory(),
+                torch.empty(p.n, p.k, dtype=p.dtype).pin_memory(),
+                torch.empty(p.n, dtype=torch.int32).pin_memory())
+
+    def run(self, As, outs, seeds=None, stream=None):
+        """Enqueue the problems (host A tensors and host output tuples) on
+        ``stream`` (default: torch's current stream); synchronise it to read
+        the outputs.  Returns the pinned info array."""
+        import torch
+        count = len(As)
+        arr = (HostProblem * max(1, count))()
+        for i, (A, (U, S, V, piv)) in enumerate(zip(As, outs)):
+            assert not A.is_cuda and A.dtype == self.plan.dtype and A.stride(1) == 1
+            arr[i] = HostProblem(A.data_ptr(), A.stride(0), 0 if seeds is None else seeds[i], U.data_ptr(),
+                                 U.stride(0), S.data_ptr(), V.data_ptr(), V.stride(0), piv.data_ptr())
+        self._infos = torch.zeros(max(1, count) * ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
+        st = torch.cuda.current_stream(self.plan.device) if stream is None else stream
+        _check(lib.ffsrqr_pipe_run(self._h, arr, count, self.device_mem.data_ptr() + self._off, self.plan.ws_ptr,
+                                   ctypes.c_void_p(st.cuda_stream),
+                                   ctypes.cast(self._infos.data_ptr(), ctypes.POINTER(Info))), "ffsrqr_pipe_run")
+        return self._infos
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.ffsrqr_pipe_destroy(h)
+            self._h = None
 
 
 class Batch:
