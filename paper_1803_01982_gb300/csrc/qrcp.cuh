@@ -70,84 +70,51 @@ __device__ __forceinline__ void qst(T *p, const QVec<T> &r) {
   else *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
 }
 
-// NC columns x_u = col0 + u * ld := (I - tau v v^T) x_u on 16-byte vectors
-// q0 .. nq - 1, and their trailing squared norms over rows > j; one warp.
-// v is zero above row j, so rows above j are left as they are.
-template <typename T, int NC>
-__device__ __forceinline__ void apply_reflector_group(T *col0, int ld, const T *v, T tau, int j, int q0, int nq,
-                                                      T *nrm_out) {
+// Step 4: H applied to the block's columns and their trailing squared norms
+// over rows > j recomputed.  v is held full length (zeros above row j), so
+// rows above j are left as they are.  LPC lanes per column: a warp takes
+// 32 / LPC columns at once and each lane a strided share of their 16-byte
+// vectors, so the dot products and norms need only log2(LPC) shuffle levels
+// (a warp per column would need five, on a chain per column).  Selected
+// columns are transformed too (their values are not used again).
+template <typename T, int LPC>
+__device__ __forceinline__ void apply_reflector_lanes(T *slab, int ld, int ncol, const T *v, T tau, int j, T *nrm) {
   constexpr int VN = QVec<T>::N;
-  const int lane = threadIdx.x & 31;
-  T w[NC], acc[NC];
-#pragma unroll
-  for (int u = 0; u < NC; ++u) w[u] = T(0);
-  for (int q = q0 + lane; q < nq; q += 32) {
-    const QVec<T> vv = qld(v + q * VN);
-#pragma unroll
-    for (int u = 0; u < NC; ++u) {
-      const QVec<T> xx = qld(col0 + (size_t)u * ld + q * VN);
-#pragma unroll
-      for (int e = 0; e < VN; ++e) w[u] = fma(vv.v[e], xx.v[e], w[u]);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int u = 0; u < NC; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
-  }
-#pragma unroll
-  for (int u = 0; u < NC; ++u) {
-    w[u] *= tau;
-    acc[u] = T(0);
-  }
-  for (int q = q0 + lane; q < nq; q += 32) {
-    const QVec<T> vv = qld(v + q * VN);
-#pragma unroll
-    for (int u = 0; u < NC; ++u) {
-      T *px = col0 + (size_t)u * ld + q * VN;
-      QVec<T> xx = qld(px);
-#pragma unroll
-      for (int e = 0; e < VN; ++e) {
-        const T y = fma(-w[u], vv.v[e], xx.v[e]);
-        xx.v[e] = y;
-        if (q * VN + e > j) acc[u] = fma(y, y, acc[u]);
-      }
-      qst(px, xx);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int u = 0; u < NC; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int u = 0; u < NC; ++u)
-      if (nrm_out[u] >= T(0)) nrm_out[u] = acc[u];  // selected columns keep their mark
-  }
-}
-
-// Step 4 over the block's ncol columns: contiguous runs per warp, in groups of
-// 8, 4, 2, 1 so that each warp keeps several independent reductions in flight.
-// Selected columns are transformed too (their values are not used again).
-template <typename T>
-__device__ __forceinline__ void apply_reflector_cols(T *slab, int ld, int ncol, const T *v, T tau, int j, T *nrm) {
-  constexpr int VN = QVec<T>::N;
-  const int wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  constexpr int CPW = 32 / LPC;  // columns per warp and pass
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int gl = lane % LPC;
   const int q0 = j / VN, nq = ld / VN;
-  const int per = (ncol + nwarp - 1) / nwarp;
-  int c = wid * per;
-  const int ce = min(ncol, c + per);
-  for (; c + 8 <= ce; c += 8) apply_reflector_group<T, 8>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
-  if (c + 4 <= ce) {
-    apply_reflector_group<T, 4>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
-    c += 4;
+  for (int base = wid * CPW; base < ncol; base += nwarp * CPW) {  // warp-uniform
+    const int c = base + lane / LPC;
+    const bool on = c < ncol;
+    T *col = slab + (size_t)(on ? c : 0) * ld;
+    T w = T(0);
+    if (on)
+      for (int q = q0 + gl; q < nq; q += LPC) {
+        const QVec<T> vv = qld(v + q * VN), xx = qld(col + q * VN);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) w = fma(vv.v[e], xx.v[e], w);
+      }
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    w *= tau;
+    T acc = T(0);
+    if (on)
+      for (int q = q0 + gl; q < nq; q += LPC) {
+        const QVec<T> vv = qld(v + q * VN);
+        QVec<T> xx = qld(col + q * VN);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          const T y = fma(-w, vv.v[e], xx.v[e]);
+          xx.v[e] = y;
+          if (q * VN + e > j) acc = fma(y, y, acc);
+        }
+        qst(col + q * VN, xx);
+      }
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (on && gl == 0 && nrm[c] >= T(0)) nrm[c] = acc;  // selected columns keep their mark
   }
-  if (c + 2 <= ce) {
-    apply_reflector_group<T, 2>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
-    c += 2;
-  }
-  if (c < ce) apply_reflector_group<T, 1>(slab + (size_t)c * ld, ld, v, tau, j, q0, nq, nrm + c);
 }
 
 template <typename T>
@@ -279,7 +246,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
       __syncthreads();
       // 4. apply H to the block's columns and recompute the unselected ones'
       //    trailing norms ||B(j+1:s, i)||^2 (tau = 0: norms only)
-      apply_reflector_cols(slab, a.s_pad, ncol, v, tau, j, nrm);
+      apply_reflector_lanes<T, 2>(slab, a.s_pad, ncol, v, tau, j, nrm);
       __syncthreads();
     }
   }
