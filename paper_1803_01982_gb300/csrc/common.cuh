@@ -24,7 +24,8 @@ enum CtlSlot : int {
   CTL_JACOBI_SWEEPS = 11,
   CTL_NONFINITE = 12,
   CTL_SWEEP_ROT0 = 16,  // rotations performed in Jacobi sweeps 0..15 (diagnostic)
-  CTL_WORDS = 32,
+  CTL_WIN_KEY = 32,     // 3 x uint64 (words 32..37): QRCP winner keys, one per step mod 3
+  CTL_WORDS = 40,
 };
 
 // Doubles kept beside the control words.

@@ -8,10 +8,14 @@
 //
 // Step j (one bounded grid barrier per step):
 //   1. every block publishes its best unselected column (largest trailing norm,
-//      ties to the lowest original index) and a copy of that column;
+//      ties to the lowest original index) and a copy of that column; in single
+//      precision the choice among blocks is one atomicMax on a 64-bit key
+//      (value bits, then the complemented index) in one of three rotating
+//      words, so after the barrier a block reads a single word;
 //   2. barrier;
-//   3. every block reduces the published candidates to the same winner p,
-//      loads the winner's column and forms the Householder reflector
+//   3. every block takes the same winner p (the key, or in double precision
+//      the reduction of the published candidates), loads the winner's column
+//      from its owner's copy and forms the Householder reflector
 //      H = I - tau v v^T from B(j:s, p) (beta = -sign(x_j) ||x||);
 //   4. each block applies H to its own unselected columns and recomputes their
 //      trailing norms ||B(j+1:s, i)||^2 exactly (no downdating).
@@ -134,6 +138,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
   const int s = a.s;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   unsigned *bar = reinterpret_cast<unsigned *>(a.ctl + CTL_BARRIER0);
+  unsigned long long *wkey = reinterpret_cast<unsigned long long *>(a.ctl + CTL_WIN_KEY);  // zero on entry
 
   // load slab (zero padding rows), initial norms
   for (int c = wid; c < ncol; c += nwarp) {
@@ -162,8 +167,16 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
     }
     block_argmax(bv, bi, red_v, red_i);
     if (threadIdx.x == 0) {
-      a.cand_val[buf * G + b] = bv;
-      a.cand_idx[buf * G + b] = bi;
+      if constexpr (sizeof(T) == 4) {
+        // single precision: the winner is one atomicMax over order-preserving
+        // keys (value bits high, ~index low: larger value, then lower index)
+        if (bi != 0x7fffffff)
+          atomicMax(wkey + j % 3, ((unsigned long long)__float_as_uint((float)bv) << 32) |
+                                      (unsigned long long)(0xffffffffu - (unsigned)bi));
+      } else {
+        a.cand_val[buf * G + b] = bv;
+        a.cand_idx[buf * G + b] = bi;
+      }
     }
     if (bi != 0x7fffffff) {
       const int lc = (int)(bi - c0);
@@ -176,29 +189,35 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
     {
       T wv = neg_inf<T>();
       int wi = 0x7fffffff, wb = -1;
-      for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        const T x = a.cand_val[buf * G + g];
-        const int ix = a.cand_idx[buf * G + g];
-        if (ix != 0x7fffffff && better(x, ix, wv, wi)) {
-          wv = x;
-          wi = ix;
+      if constexpr (sizeof(T) == 4) {
+        if (threadIdx.x == 0) {
+          const unsigned long long key = *reinterpret_cast<volatile unsigned long long *>(wkey + j % 3);
+          if (key != 0ull) {
+            wv = (T)__uint_as_float((unsigned)(key >> 32));
+            wi = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+          }
+          // the key of step j + 2: last read at step j - 1, next written after the barrier of step j + 1
+          if (b == 0) wkey[(j + 2) % 3] = 0ull;
         }
+      } else {
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+          const T x = a.cand_val[buf * G + g];
+          const int ix = a.cand_idx[buf * G + g];
+          if (ix != 0x7fffffff && better(x, ix, wv, wi)) {
+            wv = x;
+            wi = ix;
+          }
+        }
+        block_argmax(wv, wi, red_v, red_i);
       }
-      block_argmax(wv, wi, red_v, red_i);
       if (threadIdx.x == 0 && wi == 0x7fffffff) {
         // no finite candidate left (NaN input): record and skip this step
         s_win_blk = -1;
         s_win_col = -1;
         set_status(a.ctl, STATUS_NONFINITE);
       } else if (threadIdx.x == 0) {
-        // which block owns column wi
-        int lo = 0, hi = G - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if ((a.n * mid) / G <= wi) lo = mid;
-          else hi = mid - 1;
-        }
-        wb = lo;
+        // the block owning column wi: the largest b with floor(n b / G) <= wi
+        wb = (int)((((int64_t)wi + 1) * G - 1) / a.n);
         s_win_blk = wb;
         s_win_col = wi;
         if (!(wv > T(0))) set_status(a.ctl, STATUS_RANK_DEFICIENT);
