@@ -226,17 +226,18 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
       wb = s_win_blk;
       wi = s_win_col;
       if (wb < 0) continue;  // uniform across blocks: every block saw the same candidates
+      // one element of the winner column per thread (s_pad <= blockDim.x)
       const T *x = a.cand_col + ((size_t)buf * G + wb) * a.lds;
-      for (int t = threadIdx.x; t < s; t += blockDim.x) v[t] = x[t];
-      __syncthreads();
-      T ss = T(0);
-      for (int t = j + 1 + threadIdx.x; t < s; t += blockDim.x) ss += v[t] * v[t];
-      ss = block_sum(ss, red_v);
-      if (threadIdx.x == 0) {
-        const T alpha = v[j];
+      const int t = threadIdx.x;
+      const T xt = (t < s) ? x[t] : T(0);
+      if (t == 0) {
+        // the winner's trailing norm wv = ||x(j:s)||^2 is known, so the
+        // reflector needs only alpha = x(j): beta = -sign(alpha) sqrt(wv);
+        // ||x(j+1:s)||^2 = wv - alpha^2 only decides whether H = I
+        const T alpha = x[j];
         T tau = T(0), beta = alpha;
-        if (ss > T(0)) {
-          const T normx = sqrt(alpha * alpha + ss);
+        if (wv - alpha * alpha > T(0)) {
+          const T normx = sqrt(wv);
           beta = (alpha >= T(0)) ? -normx : normx;
           tau = (beta - alpha) / beta;
         }
@@ -248,19 +249,11 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
       }
       __syncthreads();
       const T tau = s_tau, beta = s_beta;
-      if (b == 0) {
-        // column j of S11: transformed pivot column above the diagonal, beta, zeros
-        for (int t = threadIdx.x; t < a.k; t += blockDim.x)
-          a.S11[(size_t)t * a.k + j] = (t < j) ? v[t] : ((t == j) ? beta : T(0));
-      }
-      __syncthreads();
-      {
-        // v as the full-length reflector: zeros above row j and in the
-        // padding, 1 at row j; rows above j then see v = 0 and stay as they are
-        const T scal = s_scal;
-        for (int t = threadIdx.x; t < a.s_pad; t += blockDim.x)
-          v[t] = (t < j || t >= s) ? T(0) : ((t == j) ? T(1) : v[t] * scal);
-      }
+      // column j of S11: transformed pivot column above the diagonal, beta, zeros
+      if (b == 0 && t < a.k) a.S11[(size_t)t * a.k + j] = (t < j) ? xt : ((t == j) ? beta : T(0));
+      // v as the full-length reflector: zeros above row j and in the padding,
+      // 1 at row j; rows above j then see v = 0 and stay as they are
+      if (t < a.s_pad) v[t] = (t < j || t >= s) ? T(0) : ((t == j) ? T(1) : xt * s_scal);
       if (b == wb && threadIdx.x == 0) nrm[wi - c0] = T(-1);  // selected
       __syncthreads();
       // 4. apply H to the block's columns and recompute the unselected ones'
