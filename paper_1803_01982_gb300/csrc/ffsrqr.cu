@@ -596,7 +596,7 @@ cudaError_t launch_jacobi_lpp(cudaStream_t st, int C, int k, const T *X, const T
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)C);
   cfg.blockDim = dim3((unsigned)round_up((int64_t)g.npair * LPP, 32));
-  cfg.dynamicSmemBytes = jac_cluster_smem(k, C, sizeof(T));
+  cfg.dynamicSmemBytes = jac_cluster_smem(k, C, sizeof(T), LPP);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -994,7 +994,7 @@ int plan_jacobi(ffsrqr_plan_s *P) {
     const JacGeom g = jac_geom(k, C, vn);
     if (cdiv(g.hb / vn, lpp) > JAC_NVL) continue;
     if (round_up((int64_t)g.npair * lpp, 32) > 512) continue;
-    if (jac_cluster_smem(k, C, sizeof(T)) + 1024 > (size_t)P->smem_optin) continue;
+    if (jac_cluster_smem(k, C, sizeof(T), lpp) + 1024 > (size_t)P->smem_optin) continue;
     int nc = 0;
     if (launch_jacobi_any<T>(nullptr, C, lpp, k, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, T(0), true,
                              &nc) == cudaSuccess &&

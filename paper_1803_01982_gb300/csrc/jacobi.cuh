@@ -421,9 +421,19 @@ __host__ __device__ inline JacGeom jac_geom(int k, int C, int VN) {
   g.nvx_ctas = (g.kp + g.hb - 1) / g.hb;                    // blocks holding rows of X
   return g;
 }
-inline size_t jac_cluster_smem(int k, int C, size_t elem) {
+// Column stride of a slab in shared memory (elements): the slab height padded
+// to a number of 16-byte vectors congruent to LPP mod 8, so that the LPP
+// consecutive vectors of the 32 / (4 LPP) columns a quarter-warp reads or
+// writes at once fall in distinct bank groups.
+__host__ __device__ inline int jac_ldcol(int hb, int VN, int lpp) {
+  int nv = hb / VN;
+  const int want = lpp & 7;
+  while ((nv & 7) != want) ++nv;
+  return nv * VN;
+}
+inline size_t jac_cluster_smem(int k, int C, size_t elem, int lpp) {
   const JacGeom g = jac_geom(k, C, 16 / (int)elem);
-  const size_t slab = ((size_t)g.kk * g.hb * elem + 15) & ~(size_t)15;
+  const size_t slab = ((size_t)g.kk * jac_ldcol(g.hb, 16 / (int)elem, lpp) * elem + 15) & ~(size_t)15;
   return slab + 2 * (size_t)C * g.npair * 4 * elem + (size_t)g.kk * elem + (size_t)g.kk * sizeof(int) + 64;
 }
 
@@ -472,13 +482,14 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
   constexpr int VN = Vec16<T>::N;
   const JacGeom g = jac_geom(k, C, VN);
   const int kk = g.kk, kp = g.kp, npair = g.npair, hb = g.hb, nxc = g.nvx_ctas;
+  const int ldc = jac_ldcol(hb, VN, LPP);                  // column stride of the slab (elements)
   const int r0 = rank * hb;                               // first stacked row of this slab
   const int nvec = max(0, min(hb, 2 * kp - r0)) / VN;     // vectors per column in the slab
   const int nvx = max(0, min(nvec, (kp - r0) / VN));      // of which rows of X
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *S = reinterpret_cast<T *>(smem_raw);                           // column c at S[c * hb]
+  T *S = reinterpret_cast<T *>(smem_raw);                           // column c at S[c * ldc]
   JacPart<T> *inbox = reinterpret_cast<JacPart<T> *>(
-      smem_raw + (((size_t)kk * hb * sizeof(T) + 15) & ~(size_t)15));  // [2][C][npair]: partials received
+      smem_raw + (((size_t)kk * ldc * sizeof(T) + 15) & ~(size_t)15));  // [2][C][npair]: partials received
   T *sig = reinterpret_cast<T *>(inbox + 2 * (size_t)C * npair);    // [kk]
   int *rnk = reinterpret_cast<int *>(sig + kk);                     // [kk]
   __shared__ __align__(8) unsigned long long s_mbar[2];             // one per round parity
@@ -489,7 +500,7 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
 
   // the slab: stacked rows r0 .. r0 + hb - 1 of [X; J] (X padded to kp rows)
   for (int e = threadIdx.x; e < kk * hb; e += blockDim.x) {
-    const int c = e / hb, gr = r0 + (e - c * hb);
+    const int c = e / hb, lr = e - c * hb, gr = r0 + lr;
     T v = T(0);
     if (c < k) {
       if (gr < kp) {
@@ -499,7 +510,7 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
         v = Jin ? Jin[(size_t)c * k + jr] : ((jr == c) ? T(1) : T(0));
       }
     }
-    S[e] = v;
+    S[(size_t)c * ldc + lr] = v;
   }
   if (threadIdx.x == 0) {
     s_rot = 0;
@@ -527,7 +538,7 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
       T al = T(0), be = T(0), ga = T(0);
       float2 a2 = make_float2(0.f, 0.f), b2 = a2, g2 = a2;  // packed partial sums (single precision)
       if (p >= 0) {
-        const T *sp = S + (size_t)p * hb, *sq = S + (size_t)q * hb;
+        const T *sp = S + (size_t)p * ldc, *sq = S + (size_t)q * ldc;
 #pragma unroll
         for (int l = 0; l < JAC_NVL; ++l) {
           if (LPP * l >= nvec) break;  // uniform: no issue slots for the unused tail
@@ -608,7 +619,7 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
         T cs, sn;
         jac_rotation(al, be, ga, tol, cs, sn);
         if (sn != T(0)) {
-          T *sp = S + (size_t)p * hb, *sq = S + (size_t)q * hb;
+          T *sp = S + (size_t)p * ldc, *sq = S + (size_t)q * ldc;
 #pragma unroll
           for (int l = 0; l < JAC_NVL; ++l) {
             if (LPP * l >= nvec) break;
@@ -667,7 +678,7 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
       for (int c = wid; c < kk; c += nwarp) {
         T acc = T(0);
         for (int v = lane; v < nvx; v += 32) {
-          const Vec16<T> x = ld16(S + (size_t)c * hb + v * VN);
+          const Vec16<T> x = ld16(S + (size_t)c * ldc + v * VN);
 #pragma unroll
           for (int u = 0; u < VN; ++u) acc = fma(x.v[u], x.v[u], acc);
         }
@@ -700,9 +711,9 @@ __global__ void __launch_bounds__(512) jacobi_cluster_kernel(const T *__restrict
     const int rk = rnk[c];
     if (gr < k) {
       const T sc = sig[c];
-      Uout[(size_t)gr * k + rk] = (sc > T(0)) ? S[(size_t)c * hb + lr] / sc : ((gr == rk) ? T(1) : T(0));
+      Uout[(size_t)gr * k + rk] = (sc > T(0)) ? S[(size_t)c * ldc + lr] / sc : ((gr == rk) ? T(1) : T(0));
     } else if (gr >= kp && gr - kp < k) {
-      Vout[(size_t)(gr - kp) * k + rk] = S[(size_t)c * hb + lr];
+      Vout[(size_t)(gr - kp) * k + rk] = S[(size_t)c * ldc + lr];
     }
   }
 }
