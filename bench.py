@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--p", type=int, default=10)
-    ap.add_argument("--e2e-steps", type=int, default=12)
+    ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", choices=["single", "batch", "hosvd", "serving"], default="single",
                     help="single: one 20000x20000 problem (default); batch: 256 uneven matrices in one graph; "
