@@ -58,9 +58,11 @@ def parse():
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batch", "hosvd", "serving"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "hosvd", "sthosvd", "hosvd-core", "serving"],
+                    default="single",
                     help="single: one 20000x20000 problem (default); batch: 256 uneven matrices in one graph; "
-                         "hosvd: the three unfoldings of a 400^3 tensor; serving: Poisson request stream")
+                         "hosvd: the three unfoldings of a 400^3 tensor; sthosvd: sequentially truncated HOSVD "
+                         "of that tensor; hosvd-core: its HOSVD with the core; serving: Poisson request stream")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     return ap.parse_args()
@@ -402,6 +404,45 @@ def run_hosvd(a):
                 3, ms, 3 * 12.0 * 400 * 160000, {})
 
 
+def run_tucker(a):
+    """Tucker approximation of the 400^3 FP32 tensor of the HOSVD workload
+    (multilinear rank 40 + N(0, 1e-4^2) noise) to ranks (40, 40, 40), p = 5,
+    one ffsrqr_tucker_run per step.
+    sthosvd (Alg. 6, order 1-2-3): Flip-Flop SRQR of the 400 x 160000,
+      400 x 16000 and 400 x 1600 unfoldings, with the permutes between them;
+      only the first unfolding (256 MB) exceeds the L2.
+    hosvd-core (Alg. 5): Flip-Flop SRQR of the three 400 x 160000 unfoldings
+      (two of them permuted copies), then the core G = X x_r U_r^T mode by mode."""
+    import torch
+
+    from paper_1803_01982_gb300 import ffsrqr, synth
+    dims, ranks = (400, 400, 400), (40, 40, 40)
+    X = synth.tucker_torch(dims, ranks, 1e-4, seed=5)
+    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    st_method = a.workload == "sthosvd"
+    t = ffsrqr.Tucker(dims, ranks, None, 5, mode, ffsrqr.TUCKER_STHOSVD if st_method else ffsrqr.TUCKER_HOSVD)
+    out = t.outputs()
+    st = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        t.run(X, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        t.run(X, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    if st_method:
+        roof = 12.0 * 400 * (160000 + 16000 + 1600)   # three reads of each unfolding
+        name = "ST-HOSVD (Alg. 6) of a 400^3 FP32 tensor to ranks (40, 40, 40), p = 5, order 1-2-3"
+    else:
+        roof = 3 * 12.0 * 400 * 160000 + 4.0 * 400 * (160000 + 16000 + 1600)  # + one read per core product
+        name = "HOSVD (Alg. 5, factors and core) of a 400^3 FP32 tensor to ranks (40, 40, 40), p = 5"
+    extra = {"gpu_launches": t.launch_count() * a.steps, "statuses": [i["status"] for i in t.infos()]}
+    _batch_line(a, f"{name}, {a.mode}", 1, ms, roof, extra)
+
+
 def run_serving(a):
     """Poisson arrivals (mean a.rate per second, a.duration seconds) of
     truncated-SVD requests like singular-value-thresholding iterates:
@@ -471,7 +512,8 @@ def run_serving(a):
 def main():
     a = parse()
     if a.workload != "single" and a.impl == "ours":
-        {"batch": run_batch, "hosvd": run_hosvd, "serving": run_serving}[a.workload](a)
+        {"batch": run_batch, "hosvd": run_hosvd, "sthosvd": run_tucker, "hosvd-core": run_tucker,
+         "serving": run_serving}[a.workload](a)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

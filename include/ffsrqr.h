@@ -365,6 +365,64 @@ int ffsrqr_server_stats(ffsrqr_server_t server, int64_t *admitted, int64_t *comp
 /* Stops the scheduler (running requests finish first) and frees the arena. */
 int ffsrqr_server_destroy(ffsrqr_server_t server);
 
+/* ------------------------------------------------------------------------ */
+/* Tucker approximations: ST-HOSVD (Alg. 6) and HOSVD (Alg. 5) on Alg. 9      */
+/* ------------------------------------------------------------------------ */
+/* A rank-(k_1, ..., k_d) Tucker approximation X ~= G x_1 U_1 ... x_d U_d of a
+ * dense tensor (Sec. 3.1), with Alg. 9 as the approximate rank-k_r SVD of
+ * every unfolding:
+ *   FFSRQR_TUCKER_STHOSVD (Alg. 6): for each mode r in the processing order,
+ *     U S V^T ~= G_(r) of the current core, U_r = U, and the core is replaced
+ *     by the tensor whose mode-r unfolding is diag(S) V^T (it shrinks along
+ *     mode r to k_r);
+ *   FFSRQR_TUCKER_HOSVD (Alg. 5): U_r from the unfolding X_(r) of the input
+ *     for every mode, then G = X x_1 U_1^T ... x_d U_d^T.
+ *
+ * Layout: the tensor X (I_1 x ... x I_d) and the core G (k_1 x ... x k_d) are
+ * dense and row-major over their modes (the last index fastest).  The
+ * unfolding of mode r has the mode-r index as its row and, as its column, the
+ * row-major linear index of the other indices in increasing mode order.  U_r
+ * is I_r x k_r row-major (leading dimension k_r).  FP32 in FFSRQR_PLAIN_FP32
+ * and FFSRQR_MIXED, FP64 in FFSRQR_FP64. */
+typedef struct ffsrqr_tucker_s *ffsrqr_tucker_t;
+
+#define FFSRQR_TUCKER_STHOSVD 0
+#define FFSRQR_TUCKER_HOSVD 1
+
+/* Plans the steps for method (FFSRQR_TUCKER_*), 2 <= d <= 8 modes: dims[d] =
+ * I_r >= 1, ranks[d] = k_r in [1, I_r], order[d] = the ST-HOSVD processing
+ * order (a permutation of 0..d-1; NULL = 0, 1, ..., d-1; ignored by the
+ * HOSVD, which factors the modes in order), oversampling p and mode for every
+ * Alg. 9 run, opts as in ffsrqr_plan.  Factor step j runs Alg. 9 on an
+ * m_j x n_j unfolding: m_j = I_r for r = order[j], n_j = the product of the
+ * other modes' current sizes (k_x for the modes the ST-HOSVD has already
+ * processed, I_x otherwise); each must meet ffsrqr_plan's requirements
+ * (k_r + p <= m_j, k_r <= n_j, k_r <= 224 in FP32).  Writes the device
+ * workspace size.  Returns 0, -1 NULL handle, -2 method, -3 d, -4 dims,
+ * -5 ranks, -6 order, -7 p, -8 mode, -10 NULL workspace_bytes, -11 a step's
+ * unfolding that ffsrqr_plan rejects, FFSRQR_STATUS_UNSUPPORTED (k_r above
+ * ffsrqr_plan's limit) or FFSRQR_STATUS_CUDA. */
+int ffsrqr_tucker_plan(ffsrqr_tucker_t *plan, int32_t method, int32_t d, const int64_t *dims,
+                       const int32_t *ranks, const int32_t *order, int32_t p, int32_t mode,
+                       const ffsrqr_opts_t *opts, size_t *workspace_bytes);
+
+/* Enqueues the method on stream.  X: device tensor (read-only).  Factor step j
+ * draws its Omega from seed + j.  U: host array of d device pointers, U[r] the
+ * I_r x k_r factor of mode r.  S: NULL, or a host array of d device pointers
+ * (each may be NULL) that receive the k_r singular values Alg. 9 returns for
+ * mode r.  core: device, k_1 x ... x k_d.  workspace: device, the planned size,
+ * 256-byte aligned.  infos: NULL or a pinned host array of d reports, one per
+ * factor step, valid after the stream is synchronised.  Returns 0, -1 NULL
+ * plan, -2 X, -4 U, -6 core, -7 workspace, an ffsrqr_run code, or
+ * FFSRQR_STATUS_CUDA if a launch fails. */
+int ffsrqr_tucker_run(ffsrqr_tucker_t plan, const void *X, uint64_t seed, void *const *U, void *const *S,
+                      void *core, void *workspace, void *stream, ffsrqr_info_t *infos);
+
+/* Kernels the last ffsrqr_tucker_run enqueued (-1 for NULL). */
+int ffsrqr_tucker_launch_count(ffsrqr_tucker_t plan);
+
+int ffsrqr_tucker_destroy(ffsrqr_tucker_t plan);
+
 #ifdef __cplusplus
 }
 #endif

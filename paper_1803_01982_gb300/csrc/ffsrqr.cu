@@ -1149,6 +1149,54 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+int project_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, const T *X, int64_t ldx, T *Gt, int64_t ldg,
+                 unsigned char *ws, cudaStream_t st) {
+  WsPtrs<T> w = ws_ptrs<T>(P, ws);
+  const int64_t m = P->m, n = P->n, ldk = P->ldk;
+  const int k = P->k, nsm = P->num_sms;
+  int rc;
+  CK(cudaMemsetAsync(ws + P->off_ctl, 0, CTL_WORDS * sizeof(int), st));
+  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(X, ldx, w.q1, ldk, m,
+                                                                                          k, nullptr);
+  CKL("copy_x");
+  if (use_tc<T>(P, A, lda)) {
+    if ((rc = tc_thin_pass(st, P, ws, true, (const float *)A, lda, (const float *)w.q1, m, (float *)w.gt)))
+      return rc;
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, Gt, ldg,
+                                                                                            n, k, nullptr);
+    CKL("copy_gt");
+    return 0;
+  }
+  return launch_gemm<T>(st, P, ws, (int)n, k, (int)m, A, lda, true, w.q1, ldk, true, Gt, ldg);
+}
+
+}  // namespace
+
+// Gt (n x k, leading dimension ldg) = A^T X for A (m x n, lda) and X (m x k,
+// ldx) with the plan's pass-2 product: the three-product TF32 split on the
+// tensor cores in FFSRQR_MIXED when A is TMA-addressable, the CUDA cores
+// otherwise.  The mode products of the HOSVD core (Alg. 5) use it.  Writes
+// the number of kernels enqueued to *launches.
+int ffq_project(ffsrqr_plan_t P, const void *A, int64_t lda, const void *X, int64_t ldx, void *Gt, int64_t ldg,
+                void *workspace, cudaStream_t st, int *launches) {
+  g_launches = 0;
+  unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
+  int rc;
+  if (P->elem == 8)
+    rc = project_impl<double>(P, (const double *)A, lda, (const double *)X, ldx, (double *)Gt, ldg, ws, st);
+  else
+    rc = project_impl<float>(P, (const float *)A, lda, (const float *)X, ldx, (float *)Gt, ldg, ws, st);
+  *launches = g_launches;
+  return rc;
+}
+
+extern "C" {
+
 int ffsrqr_plan_shape(ffsrqr_plan_t plan, int64_t *m, int64_t *n, int32_t *k, int32_t *p, int32_t *mode) {
   if (!plan) return -1;
   if (m) *m = plan->m;

@@ -130,6 +130,15 @@ def _load():
     lib.ffsrqr_plan_shape.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.ffsrqr_plan_shape.restype = ctypes.c_int
+    lib.ffsrqr_tucker_plan.argtypes = [ctypes.POINTER(P), i32, i32, P, P, P, i32, i32, ctypes.POINTER(Opts),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_tucker_plan.restype = ctypes.c_int
+    lib.ffsrqr_tucker_run.argtypes = [P, P, u64, P, P, P, P, P, P]
+    lib.ffsrqr_tucker_run.restype = ctypes.c_int
+    lib.ffsrqr_tucker_launch_count.argtypes = [P]
+    lib.ffsrqr_tucker_launch_count.restype = ctypes.c_int
+    lib.ffsrqr_tucker_destroy.argtypes = [P]
+    lib.ffsrqr_tucker_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -163,6 +172,12 @@ ffsrqr_pipe_create = lib.ffsrqr_pipe_create
 ffsrqr_pipe_run = lib.ffsrqr_pipe_run
 ffsrqr_pipe_destroy = lib.ffsrqr_pipe_destroy
 ffsrqr_plan_shape = lib.ffsrqr_plan_shape
+ffsrqr_tucker_plan = lib.ffsrqr_tucker_plan
+ffsrqr_tucker_run = lib.ffsrqr_tucker_run
+ffsrqr_tucker_launch_count = lib.ffsrqr_tucker_launch_count
+ffsrqr_tucker_destroy = lib.ffsrqr_tucker_destroy
+TUCKER_STHOSVD = 0
+TUCKER_HOSVD = 1
 
 
 class FfsrqrError(RuntimeError):
@@ -442,3 +457,75 @@ class Server:
     def __del__(self):
         self.close()
 
+
+
+class Tucker:
+    """Plan + device workspace for a rank-``ranks`` Tucker approximation of a
+    dims[0] x ... x dims[d-1] tensor: ``method`` TUCKER_STHOSVD (Alg. 6, in
+    ``order``) or TUCKER_HOSVD (Alg. 5), with Flip-Flop SRQR (oversampling p,
+    ``mode``) for every unfolding."""
+
+    def __init__(self, dims, ranks, order=None, p: int = 5, mode: int = PLAIN_FP32,
+                 method: int = TUCKER_STHOSVD, g: float = 2.0, device=None):
+        import torch
+        self.d = len(dims)
+        self.dims, self.ranks = [int(x) for x in dims], [int(x) for x in ranks]
+        self.order = list(range(self.d)) if order is None else [int(x) for x in order]
+        self.p, self.mode, self.method = p, mode, method
+        self.device = torch.device("cuda" if device is None else device)
+        self.dtype = torch.float64 if mode == FP64 else torch.float32
+        d = self.d
+        dims_c = (ctypes.c_int64 * d)(*self.dims)
+        ranks_c = (ctypes.c_int32 * d)(*self.ranks)
+        order_c = (ctypes.c_int32 * d)(*self.order)
+        opts = Opts(g, 4 * max(self.ranks), 0)
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        with torch.cuda.device(self.device):
+            _check(lib.ffsrqr_tucker_plan(ctypes.byref(self._h), method, d, dims_c, ranks_c, order_c, p, mode,
+                                          ctypes.byref(opts), ctypes.byref(ws)), "ffsrqr_tucker_plan")
+        self.workspace_bytes = ws.value
+        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        self._ws_off = (-self.workspace.data_ptr()) % 256
+        self._info_host = torch.zeros(d * ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
+
+    @property
+    def ws_ptr(self) -> int:
+        return self.workspace.data_ptr() + self._ws_off
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.ffsrqr_tucker_destroy(h)
+            self._h = None
+
+    def outputs(self):
+        """(U_r by mode, S_r by mode, core) as torch device tensors."""
+        import torch
+        kw = {"dtype": self.dtype, "device": self.device}
+        Us = [torch.empty(I, k, **kw) for I, k in zip(self.dims, self.ranks)]
+        Ss = [torch.empty(k, **kw) for k in self.ranks]
+        core = torch.empty(*self.ranks, **kw)
+        return Us, Ss, core
+
+    def run(self, X, seed: int = 0, out=None, stream=None):
+        """Enqueue ffsrqr_tucker_run on ``stream`` (default: torch's current stream)."""
+        import torch
+        assert X.is_cuda and X.dtype == self.dtype and list(X.shape) == self.dims and X.is_contiguous()
+        Us, Ss, core = out if out is not None else self.outputs()
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        u_c = (ctypes.c_void_p * self.d)(*[u.data_ptr() for u in Us])
+        s_c = (ctypes.c_void_p * self.d)(*[s.data_ptr() for s in Ss])
+        _check(lib.ffsrqr_tucker_run(self._h, X.data_ptr(), seed, u_c, s_c, core.data_ptr(), self.ws_ptr,
+                                     ctypes.c_void_p(st.cuda_stream), self._info_host.data_ptr()),
+               "ffsrqr_tucker_run")
+        return Us, Ss, core
+
+    def infos(self):
+        """Per-factor-step reports of the last run (after a sync)."""
+        raw = bytes(self._info_host.numpy().tobytes())
+        sz = ctypes.sizeof(Info)
+        return [Info.from_buffer_copy(raw[j * sz:(j + 1) * sz]).as_dict() for j in range(self.d)]
+
+    def launch_count(self) -> int:
+        return lib.ffsrqr_tucker_launch_count(self._h)

@@ -14,6 +14,8 @@ matrix with diag(R) > 0, which makes Q unique):
 * ``decayed(m, n, sigma, noise, seed)``:  A = U_r diag(sigma) V_r^T + noise*E
 * ``kahan(n, c)``:                          Kahan's upper-triangular matrix
 * ``rank_k(m, n, k, seed)``:                X_L X_R^T with Gaussian factors
+* ``tucker(dims, core, decay, noise, seed)``: C x_1 Q_1 ... x_d Q_d + noise*E,
+  C Gaussian, optionally graded by decay[r]^{i_r} along each mode
 """
 from __future__ import annotations
 
@@ -93,3 +95,46 @@ def slow_decay(r: int) -> np.ndarray:
 
 def fast_decay(r: int, base: float = 0.97) -> np.ndarray:
     return base ** np.arange(1, r + 1, dtype=np.float64)
+
+
+def _tucker_core(rng, core, decay):
+    C = rng.standard_normal(tuple(core))
+    if decay is not None:
+        for r, c in enumerate(decay):
+            shape = [1] * len(core)
+            shape[r] = core[r]
+            C = C * (float(c) ** np.arange(core[r])).reshape(shape)
+    return C
+
+
+def tucker(dims, core, decay=None, noise: float = 0.0, seed: int = 1, dtype=np.float32) -> np.ndarray:
+    """X = C x_1 Q_1 ... x_d Q_d + noise * E (row-major over the modes), built in
+    FP64 and rounded once.  C (core[0] x ... x core[d-1]) is Gaussian, scaled by
+    decay[r]^{i_r} along mode r when decay is given; Q_r is dims[r] x core[r]
+    orthonormal.  The multilinear rank is core when noise = 0."""
+    rng = np.random.default_rng(seed)
+    X = _tucker_core(rng, core, decay)
+    for r, (I, c) in enumerate(zip(dims, core)):
+        Q = orthonormal(rng, I, c)
+        X = np.moveaxis(np.tensordot(Q, X, axes=([1], [r])), 0, r)
+    if noise:
+        X = X + noise * rng.standard_normal(tuple(dims))
+    return np.ascontiguousarray(X.astype(dtype))
+
+
+def tucker_torch(dims, core, noise: float, seed: int, device: str = "cuda"):
+    """``tucker`` (no grading) formed on the device in FP64 with torch's seeded
+    generator for the noise, rounded once to FP32; for tensors too large to
+    assemble on the host.  Input synthesis only."""
+    import torch
+    rng = np.random.default_rng(seed)
+    X = torch.from_numpy(_tucker_core(rng, core, None)).to(device)
+    for r, (I, c) in enumerate(zip(dims, core)):
+        Q = torch.from_numpy(orthonormal(rng, I, c)).to(device)
+        X = torch.movedim(torch.tensordot(Q, X, dims=([1], [r])), 0, r)
+    X = X.contiguous()
+    if noise:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
+        X += noise * torch.randn(X.shape, generator=gen, device=device, dtype=torch.float64)
+    return X.to(torch.float32).contiguous()
