@@ -138,3 +138,17 @@ def tucker_torch(dims, core, noise: float, seed: int, device: str = "cuda"):
         gen.manual_seed(seed)
         X += noise * torch.randn(X.shape, generator=gen, device=device, dtype=torch.float64)
     return X.to(torch.float32).contiguous()
+
+
+def rpca_problem(m: int, n: int, rank: int, nnz: int, seed: int = 1, dtype=np.float32):
+    """Robust PCA test matrix of Sec. 4.3.1: M = X* + E*, X* = X_L X_R^T with
+    Gaussian X_L (m x rank) and X_R (n x rank), E* with nnz entries at
+    uniformly random positions, values uniform in [-500, 500].  Returns
+    (M, X*, E*), built in FP64 and rounded once."""
+    rng = np.random.default_rng(seed)
+    Xs = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n))
+    Es = np.zeros((m, n))
+    idx = rng.choice(m * n, size=nnz, replace=False)
+    Es.flat[idx] = rng.uniform(-500.0, 500.0, size=nnz)
+    M = Xs + Es
+    return (np.ascontiguousarray(M.astype(dtype)), Xs.astype(dtype), Es.astype(dtype))
