@@ -423,6 +423,81 @@ int ffsrqr_tucker_launch_count(ffsrqr_tucker_t plan);
 
 int ffsrqr_tucker_destroy(ffsrqr_tucker_t plan);
 
+/* ------------------------------------------------------------------------ */
+/* Robust PCA by IALM (Alg. 7) on Alg. 9                                     */
+/* ------------------------------------------------------------------------ */
+/* min ||X||_* + lambda ||E||_1 subject to M = X + E (Sec. 3.2), by the
+ * inexact augmented Lagrange multiplier iteration of Alg. 7 with Alg. 9 as
+ * the truncated SVD of M - E + Y/mu at a predicted rank sv.  Start:
+ * J = max(||M||_2, ||M||_max) (||M||_2 = the first singular value of Alg. 9
+ * on M at rank sv0), Y = M / J, E = 0, mu = 1.25 / ||M||_2.  Per iteration:
+ * X = U S_{1/mu}(S) V^T over the svp singular values above 1/mu;
+ * E = S_{lambda/mu}(M - X + Y/mu); Y += mu (M - X - E); mu = min(rho mu,
+ * mu_bar), mu_bar = mu_bar_ratio * mu0; stop when ||M - X - E||_F <
+ * tol ||M||_F.  Predicted rank: sv0 at first; then svp + 1 if svp < sv, else
+ * svp + round(0.05 n); at most kmax. */
+typedef struct ffsrqr_rpca_s *ffsrqr_rpca_t;
+
+/* Options; a field <= 0 takes its default: mode as given (FFSRQR_*; NULL
+ * options = FFSRQR_MIXED), p = 10, sv0 = 10, max_iter = 100, kmax = the
+ * largest rank the mode supports (224 FP32, 160 FP64, and at most
+ * min(n, m - p)), lambda = 1/sqrt(max(m, n)), rho = 1.5 (values <= 1 take it
+ * too), mu_bar_ratio = 1e7, tol = 1e-6 in the FP32 modes and 1e-7 in FP64
+ * (an FP32 residual does not resolve 1e-7 of ||M||_F). */
+typedef struct {
+  int32_t mode;
+  int32_t p;
+  int32_t sv0;
+  int32_t max_iter;
+  int32_t kmax;
+  int32_t reserved;
+  double lambda;
+  double rho;
+  double mu_bar_ratio;
+  double tol;
+} ffsrqr_rpca_opts_t;
+
+/* Result of a run: status 0 (converged) or FFSRQR_STATUS_SWAP_CAP (the
+ * iteration cap was reached), iterations, rank of X (svp of the last
+ * iteration), the relative residual ||M - X - E||_F / ||M||_F, the nonzeros
+ * of E, ||M||_2 and lambda as used. */
+typedef struct {
+  int32_t status;
+  int32_t iters;
+  int32_t rank;
+  int32_t reserved;
+  double rel_residual;
+  int64_t nnz_e;
+  double norm2;
+  double lambda;
+} ffsrqr_rpca_info_t;
+
+/* Plans a solver for m x n inputs (m, n >= 2) and writes the device
+ * workspace size (the largest Alg. 9 plan's workspace plus Y, Z (m x n each),
+ * U, S, V, piv).  Alg. 9 plans for other ranks are made on first use and
+ * cached.  Returns 0, -1 NULL handle, -2 m, -3 n, -4 options (mode, negative
+ * values, or no admissible rank), -5 NULL workspace_bytes, or the
+ * ffsrqr_plan status for the largest rank. */
+int ffsrqr_rpca_create(ffsrqr_rpca_t *solver, int64_t m, int64_t n, const ffsrqr_rpca_opts_t *opts,
+                       size_t *workspace_bytes);
+
+/* Solves for M (device, m x n row-major, ldm >= n; FP32, FP64 in FFSRQR_FP64)
+ * into X and E (device, m x n, ldx, lde >= n).  Blocking: the host reads the
+ * singular values and the residual back every iteration (the rank rule and
+ * the stopping test need them) and returns when the iteration ends.  Alg. 9
+ * run i draws its Omega from seed + i (run 0 estimates ||M||_2).  info (host,
+ * may be NULL) receives the result.  Returns 0, -1 NULL solver, -2 M, -3 ldm,
+ * -4 X, -5 ldx, -6 E, -7 lde, -9 workspace, an ffsrqr_plan / ffsrqr_run code,
+ * FFSRQR_STATUS_TIMEOUT or FFSRQR_STATUS_NONFINITE when an Alg. 9 run
+ * reports it, or FFSRQR_STATUS_CUDA. */
+int ffsrqr_rpca_run(ffsrqr_rpca_t solver, const void *M, int64_t ldm, void *X, int64_t ldx, void *E,
+                    int64_t lde, uint64_t seed, void *workspace, void *stream, ffsrqr_rpca_info_t *info);
+
+/* Kernels the last ffsrqr_rpca_run enqueued (-1 for NULL). */
+int ffsrqr_rpca_launch_count(ffsrqr_rpca_t solver);
+
+int ffsrqr_rpca_destroy(ffsrqr_rpca_t solver);
+
 #ifdef __cplusplus
 }
 #endif

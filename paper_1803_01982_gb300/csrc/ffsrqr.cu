@@ -1195,6 +1195,25 @@ int ffq_project(ffsrqr_plan_t P, const void *A, int64_t lda, const void *X, int6
   return rc;
 }
 
+// X (m x n, ldx) = U V^T over the first r columns of U (m x r, ldu) and V
+// (n x r, ldv), on the CUDA cores (r <= the plan's k), for the singular value
+// thresholding step of the robust PCA driver (Alg. 7).  Writes the number of
+// kernels enqueued to *launches.
+int ffq_gemm_nt(ffsrqr_plan_t P, int64_t m, int64_t n, int r, const void *U, int64_t ldu, const void *V,
+                int64_t ldv, void *X, int64_t ldx, void *workspace, cudaStream_t st, int *launches) {
+  g_launches = 0;
+  unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
+  int rc;
+  if (P->elem == 8)
+    rc = launch_gemm<double>(st, P, ws, (int)m, (int)n, r, (const double *)U, ldu, false, (const double *)V, ldv,
+                             false, (double *)X, ldx);
+  else
+    rc = launch_gemm<float>(st, P, ws, (int)m, (int)n, r, (const float *)U, ldu, false, (const float *)V, ldv,
+                            false, (float *)X, ldx);
+  *launches = g_launches;
+  return rc;
+}
+
 extern "C" {
 
 int ffsrqr_plan_shape(ffsrqr_plan_t plan, int64_t *m, int64_t *n, int32_t *k, int32_t *p, int32_t *mode) {

@@ -63,6 +63,24 @@ class HostProblem(ctypes.Structure):
                 ("V", ctypes.c_void_p), ("ldv", ctypes.c_int64), ("piv", ctypes.c_void_p)]
 
 
+class RpcaOpts(ctypes.Structure):
+    """ffsrqr_rpca_opts_t."""
+    _fields_ = [("mode", ctypes.c_int32), ("p", ctypes.c_int32), ("sv0", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("kmax", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lambda_", ctypes.c_double), ("rho", ctypes.c_double), ("mu_bar_ratio", ctypes.c_double),
+                ("tol", ctypes.c_double)]
+
+
+class RpcaInfo(ctypes.Structure):
+    """ffsrqr_rpca_info_t."""
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("nnz_e", ctypes.c_int64),
+                ("norm2", ctypes.c_double), ("lambda_", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -139,6 +157,15 @@ def _load():
     lib.ffsrqr_tucker_launch_count.restype = ctypes.c_int
     lib.ffsrqr_tucker_destroy.argtypes = [P]
     lib.ffsrqr_tucker_destroy.restype = ctypes.c_int
+    lib.ffsrqr_rpca_create.argtypes = [ctypes.POINTER(P), i64, i64, ctypes.POINTER(RpcaOpts),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_rpca_create.restype = ctypes.c_int
+    lib.ffsrqr_rpca_run.argtypes = [P, P, i64, P, i64, P, i64, u64, P, P, ctypes.POINTER(RpcaInfo)]
+    lib.ffsrqr_rpca_run.restype = ctypes.c_int
+    lib.ffsrqr_rpca_launch_count.argtypes = [P]
+    lib.ffsrqr_rpca_launch_count.restype = ctypes.c_int
+    lib.ffsrqr_rpca_destroy.argtypes = [P]
+    lib.ffsrqr_rpca_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -176,6 +203,10 @@ ffsrqr_tucker_plan = lib.ffsrqr_tucker_plan
 ffsrqr_tucker_run = lib.ffsrqr_tucker_run
 ffsrqr_tucker_launch_count = lib.ffsrqr_tucker_launch_count
 ffsrqr_tucker_destroy = lib.ffsrqr_tucker_destroy
+ffsrqr_rpca_create = lib.ffsrqr_rpca_create
+ffsrqr_rpca_run = lib.ffsrqr_rpca_run
+ffsrqr_rpca_launch_count = lib.ffsrqr_rpca_launch_count
+ffsrqr_rpca_destroy = lib.ffsrqr_rpca_destroy
 TUCKER_STHOSVD = 0
 TUCKER_HOSVD = 1
 
@@ -529,3 +560,48 @@ class Tucker:
 
     def launch_count(self) -> int:
         return lib.ffsrqr_tucker_launch_count(self._h)
+
+
+class RPCA:
+    """Robust PCA solver (Alg. 7, IALM with Alg. 9 as the truncated SVD) for
+    m x n inputs, with its device workspace.  Options left at 0 take the C
+    ABI's defaults (ffsrqr_rpca_opts_t)."""
+
+    def __init__(self, m: int, n: int, mode: int = MIXED, p: int = 0, sv0: int = 0, max_iter: int = 0,
+                 kmax: int = 0, lam: float = 0.0, rho: float = 0.0, mu_bar_ratio: float = 0.0, tol: float = 0.0,
+                 device=None):
+        import torch
+        self.m, self.n, self.mode = m, n, mode
+        self.device = torch.device("cuda" if device is None else device)
+        self.dtype = torch.float64 if mode == FP64 else torch.float32
+        opts = RpcaOpts(mode, p, sv0, max_iter, kmax, 0, lam, rho, mu_bar_ratio, tol)
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        with torch.cuda.device(self.device):
+            _check(lib.ffsrqr_rpca_create(ctypes.byref(self._h), m, n, ctypes.byref(opts), ctypes.byref(ws)),
+                   "ffsrqr_rpca_create")
+        self.workspace_bytes = ws.value
+        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        self._ws_off = (-self.workspace.data_ptr()) % 256
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.ffsrqr_rpca_destroy(h)
+            self._h = None
+
+    def run(self, M, X=None, E=None, seed: int = 0, stream=None):
+        """Solve for M (device, m x n); returns (X, E, info dict).  Blocking."""
+        import torch
+        assert M.is_cuda and M.dtype == self.dtype and M.shape == (self.m, self.n) and M.stride(1) == 1
+        X = torch.empty_like(M) if X is None else X
+        E = torch.empty_like(M) if E is None else E
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        info = RpcaInfo()
+        _check(lib.ffsrqr_rpca_run(self._h, M.data_ptr(), M.stride(0), X.data_ptr(), X.stride(0), E.data_ptr(),
+                                   E.stride(0), seed, self.workspace.data_ptr() + self._ws_off,
+                                   ctypes.c_void_p(st.cuda_stream), ctypes.byref(info)), "ffsrqr_rpca_run")
+        return X, E, info.as_dict()
+
+    def launch_count(self) -> int:
+        return lib.ffsrqr_rpca_launch_count(self._h)
