@@ -434,7 +434,9 @@ int ffsrqr_tucker_destroy(ffsrqr_tucker_t plan);
  * X = U S_{1/mu}(S) V^T over the svp singular values above 1/mu;
  * E = S_{lambda/mu}(M - X + Y/mu); Y += mu (M - X - E); mu = min(rho mu,
  * mu_bar), mu_bar = mu_bar_ratio * mu0; stop when ||M - X - E||_F <
- * tol ||M||_F.  Predicted rank: sv0 at first; then svp + 1 if svp < sv, else
+ * tol ||M||_F, or when it stalls (falls by less than 10 % in an iteration)
+ * below 100 tol: the rounding floor of the FP32 truncated SVD lies near
+ * 1e-6 ||M||_F at 2000 x 2000.  Predicted rank: sv0 at first; then svp + 1 if svp < sv, else
  * svp + round(0.05 n); at most kmax. */
 typedef struct ffsrqr_rpca_s *ffsrqr_rpca_t;
 

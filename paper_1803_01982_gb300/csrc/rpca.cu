@@ -8,7 +8,9 @@
 //   X = U S_{1/mu}(S) V^T            (the svp singular values above 1/mu)
 //   E = S_{lambda/mu}(M - X + Y/mu)  (entrywise soft shrinkage)
 //   Y = Y + mu (M - X - E),  mu = min(rho mu, mu_bar)
-// until ||M - X - E||_F < tol ||M||_F.  One fused kernel does the E, Y and
+// until ||M - X - E||_F < tol ||M||_F, or until the residual stalls below
+// 100 tol (its rounding floor; the FP32 modes reach it near 1e-6 at 2000^2).
+// One fused kernel does the E, Y and
 // residual updates and already writes the next iteration's Z, so each
 // iteration reads M, X, Y once and writes E, Y, Z once besides Alg. 9 and the
 // rank-svp product X = U' V^T.  The host reads S and two scalars back per
@@ -302,11 +304,15 @@ int rpca_impl(ffsrqr_rpca_s *R, const T *M, int64_t ldm, T *X, int64_t ldx, T *E
     ++launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("rpca update", e);
     if ((rc = fetch_stats())) return rc;
+    const double rel_prev = rel;
     rel = std::sqrt(hs.sumsq) / normM;
     nnz = hs.count;
     mu = mu_next;
     sv = sv_next;
-    if (rel < R->tol) {
+    // converged: below tol, or stalled below 100 tol (the residual has reached
+    // the rounding floor of the truncated SVD, about 1e-6 of ||M||_F in FP32 at
+    // 2000 x 2000; iterating on lets noise singular values pass 1/mu)
+    if (rel < R->tol || (it > 1 && rel < 100.0 * R->tol && rel > 0.9 * rel_prev)) {
       status = 0;
       break;
     }

@@ -76,6 +76,21 @@ def test_paper_size_1000_mixed():
     assert np.linalg.norm(X - Xs) <= 1e-5 * np.linalg.norm(Xs)
 
 
+def test_paper_size_2000_mixed():
+    """The second table row: rank 200, near the largest rank this build runs
+    (the predicted rank peaks at 224), and an FP32 residual floor near 1e-6
+    of ||M||_F that the stall rule stops at."""
+    rows = [list(map(float, l.split())) for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    m, n, err_p, it_p, nnz_p, sv_p = rows[1]
+    M, Xs, Es = problem(int(m))
+    _, X, E, info = run_gpu(M, ffsrqr.MIXED)
+    assert info["status"] == 0
+    assert info["rank"] == int(sv_p)
+    assert abs(info["nnz_e"] - nnz_p) <= 0.002 * nnz_p
+    assert abs(info["iters"] - it_p) <= 6
+    assert np.linalg.norm(X - Xs) <= 1e-5 * np.linalg.norm(Xs)
+
+
 def test_zero_matrix_and_arguments():
     import ctypes
     s = ffsrqr.RPCA(64, 48, ffsrqr.PLAIN_FP32)
