@@ -211,6 +211,24 @@ def config(a):
             "mode": a.mode, "l2": l2, "parallelism": f"replicas x{a.gpus}"}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The contract's timing rule across replicas: the max of a per-rank
+    scalar over all ranks (x itself on a single rank).  device: where the
+    collective's tensor lives (a CUDA device for NCCL, "cpu" for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each replica factors its own matrix of the same recipe."""
+    return 1 + rank
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -220,7 +238,7 @@ def run_ours(a, rank, world, local_rank):
     torch.cuda.set_device(dev)
     mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
     r = min(2000, a.m, a.n)
-    A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=1 + rank, device=str(dev))
+    A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=replica_seed(rank), device=str(dev))
     plan = ffsrqr.Plan(a.m, a.n, a.k, a.p, mode, flags=ffsrqr.FLAG_PHASE_TIMES, device=dev)
     out = plan.outputs()
     st = torch.cuda.current_stream(dev)
@@ -250,11 +268,7 @@ def run_ours(a, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     clocks = clocks_stop(clk, clk_path)
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
     info = plan.info()
     value = world * 1000.0 / ms
     phases = {k: v / a.steps for k, v in phase_sum.items()}
@@ -292,11 +306,7 @@ def run_ours(a, rank, world, local_rank):
         pipe.run([Ah] * a.e2e_steps, [host_out[i % 2] for i in range(a.e2e_steps)], stream=st)
         e1.record(st)
         torch.cuda.synchronize(dev)
-        ems = e0.elapsed_time(e1) / a.e2e_steps
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1) / a.e2e_steps, dev)
         d2h = sum(t.numel() * t.element_size() for t in out)
         e2e = {"value": world * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 4,
                "d2h_bytes_per_step": d2h, "ms_per_step": ems}
