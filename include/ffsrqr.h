@@ -100,13 +100,28 @@ typedef struct {
 int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
                 const ffsrqr_opts_t *opts, size_t *workspace_bytes);
 
+/* The same with Alg. 9's SRQR depth l >= k as an argument (Sec. 3.2: "l is
+ * usually a little larger than k, like l = k + 5"): SRQR runs to l steps on
+ * the sketch of l + p rows, V' has l columns, the SVD of A Pi Qhat_1 (m x l)
+ * is computed, and its leading k singular triplets are returned.  ffsrqr_plan
+ * is this with l = k.  Requirements as ffsrqr_plan's with l in place of k,
+ * and 1 <= k <= l.  The workspace adds the depth-l U, S and V.  Errors: -1
+ * plan NULL, -2 m, -3 n, -4 k, -5 l, -6 p, -7 mode, -8 opts, -9
+ * workspace_bytes NULL, and the statuses of ffsrqr_plan. */
+int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t l, int32_t p, int32_t mode,
+                  const ffsrqr_opts_t *opts, size_t *workspace_bytes);
+
+/* SRQR depth l of a plan (k for plans made by ffsrqr_plan); -1 for NULL. */
+int ffsrqr_plan_depth(ffsrqr_plan_t plan);
+
 /* Run Alg. 9 on A (device, m x n, row-major, lda >= n; FP32, or FP64 in
  * FFSRQR_FP64 mode) and write
  *   U   (device, m x k, row-major, ldu >= k),
  *   S   (device, k, descending),
  *   V   (device, n x k, row-major, ldv >= k),
- *   piv (device, int32[n]): piv[0:k] = the final selected columns of A (0-based,
- *        in R order); piv[k:n] = the remaining columns in ascending order.
+ *   piv (device, int32[n]): piv[0:l] = the final selected columns of A (0-based,
+ *        in R order; l = k unless planned by ffsrqr_plan_l); piv[l:n] = the
+ *        remaining columns in ascending order.
  * Omega is generated on the device from seed (Philox4x32-10, stream 0).
  * workspace: device, >= the size reported by ffsrqr_plan, 256-byte aligned.
  * stream: a cudaStream_t (NULL = legacy default stream).  The call only
@@ -301,8 +316,8 @@ int ffsrqr_pipe_run(ffsrqr_pipe_t pipe, const ffsrqr_host_problem_t *probs, int3
 
 int ffsrqr_pipe_destroy(ffsrqr_pipe_t pipe);
 
-/* Shape of a plan: m, n, k, p, mode (any pointer may be NULL).  Returns 0, or
- * -1 for a NULL plan. */
+/* Shape of a plan: m, n, k (the rank returned), p, mode (any pointer may be
+ * NULL).  Returns 0, or -1 for a NULL plan. */
 int ffsrqr_plan_shape(ffsrqr_plan_t plan, int64_t *m, int64_t *n, int32_t *k, int32_t *p, int32_t *mode);
 
 /* ------------------------------------------------------------------------ */

@@ -208,8 +208,15 @@ class FfsrqrResult:
 
 
 def ffsrqr(A, k: int, p: int, seed: int = 0, g: float = 2.0, max_swaps: int | None = None,
-           trace: bool = False) -> FfsrqrResult:
-    """Alg. 9 in FP64 on A (any float array, upcast to float64)."""
+           trace: bool = False, l: int | None = None) -> FfsrqrResult:
+    """Alg. 9 in FP64 on A (any float array, upcast to float64).  l (>= k) is
+    the SRQR depth: SRQR and the SVD of A Pi Qhat_1 run at depth l, and the
+    leading k singular triplets are returned (Alg. 9's U_k, Sigma_k, V_k)."""
+    if l is not None and l != k:
+        assert l > k
+        r = ffsrqr(A, l, p, seed, g, max_swaps, trace)
+        r.U, r.S, r.V = r.U[:, :k].copy(), r.S[:k].copy(), r.V[:, :k].copy()
+        return r
     A = _f64(A)
     m, n = A.shape
     s = k + p

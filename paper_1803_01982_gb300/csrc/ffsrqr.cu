@@ -82,6 +82,8 @@ void ffq_set_last_error(const char *what, cudaError_t e) { cuda_ok(e, what); }
 struct ffsrqr_plan_s {
   int64_t m, n;
   int k, p, s, mode;
+  int kout;                       // rank returned (Alg. 9's k); k above is the SRQR depth l >= kout
+  size_t off_uo, off_so, off_vo;  // l > kout: the depth-l U, S, V before truncation
   double g;
   int max_swaps, flags;
   int device, num_sms;
@@ -863,6 +865,28 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   return 0;
 }
 
+// Alg. 9 with SRQR depth l = P->k above the target rank kout: the depth-l
+// U, S, V go to the workspace and their leading kout columns to the caller.
+template <typename T>
+int run_truncated(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
+                  int64_t ldv, int32_t *piv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
+  const int64_t m = P->m, n = P->n;
+  const int l = P->k, k = P->kout, nsm = P->num_sms;
+  T *uo = reinterpret_cast<T *>(ws + P->off_uo);
+  T *so = reinterpret_cast<T *>(ws + P->off_so);
+  T *vo = reinterpret_cast<T *>(ws + P->off_vo);
+  int rc;
+  if ((rc = run_impl<T>(P, A, lda, seed, uo, l, so, vo, l, piv, ws, st, info))) return rc;
+  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(uo, l, U, ldu, m, k,
+                                                                                          nullptr);
+  CKL("copy_u");
+  copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(vo, l, V, ldv, n, k,
+                                                                                          nullptr);
+  CKL("copy_v");
+  CK(cudaMemcpyAsync(S, so, (size_t)k * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  return 0;
+}
+
 template <typename T>
 void layout(ffsrqr_plan_s *P) {
   const int64_t m = P->m, n = P->n;
@@ -943,6 +967,14 @@ void layout(ffsrqr_plan_s *P) {
   } else {
     P->off_tcpart = P->off_tt = P->off_bh = P->off_bl = 0;
     P->off_sinv = P->off_sh = P->off_sl = P->off_scr = 0;
+  }
+  if (P->kout < k) {
+    P->off_uo = off;
+    off = align256(off + (size_t)m * k * E);
+    P->off_so = off;
+    off = align256(off + (size_t)k * E);
+    P->off_vo = off;
+    off = align256(off + (size_t)n * k * E);
   }
   P->ws_bytes = off;
   auto item = [&](int i, size_t o, int64_t r, int64_t c, int64_t ld) {
@@ -1050,16 +1082,28 @@ extern "C" {
 
 int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
                 const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  return ffsrqr_plan_l(plan, m, n, k, k, p, mode, opts, workspace_bytes);
+}
+
+int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32_t k, int32_t p, int32_t mode,
+                  const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  // here k is Alg. 9's SRQR depth l and kout its target rank; the checks
+  // below use ffsrqr_plan's argument numbers, shifted by one after kout
   if (!plan) return -1;
   *plan = nullptr;
+  if (kout < 1 || kout > k) {
+    if (k >= 1 && kout > k) return -5;
+    return -4;
+  }
   if (m < 1 || m > (int64_t)INT32_MAX) return -2;
   if (n < 1 || n > (int64_t)INT32_MAX) return -3;
-  if (k < 1 || k > n || k > m) return -4;
-  if (p < 0 || (int64_t)k + p > m || k + p > 256) return -5;
-  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -6;
-  if (opts && !(opts->g > 1.0)) return -7;
-  if (opts && opts->max_swaps < 0) return -7;
-  if (!workspace_bytes) return -8;
+  const int sh = (kout == k) ? 0 : 1;  // ffsrqr_plan has no l argument
+  if (k < 1 || k > n || k > m) return -4 - sh;
+  if (p < 0 || (int64_t)k + p > m || k + p > 256) return -5 - sh;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -6 - sh;
+  if (opts && !(opts->g > 1.0)) return -7 - sh;
+  if (opts && opts->max_swaps < 0) return -7 - sh;
+  if (!workspace_bytes) return -8 - sh;
   const int elem = (mode == FFSRQR_FP64) ? 8 : 4;
   // the k x k factors live in one block's shared memory, and the row solves
   // hold at most 7 x 32 columns per lane group
@@ -1069,6 +1113,7 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
   P->m = m;
   P->n = n;
   P->k = k;
+  P->kout = kout;
   P->p = p;
   P->s = k + p;
   P->mode = mode;
@@ -1127,10 +1172,10 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   if (!A) return -2;
   if (lda < plan->n) return -3;
   if (!U) return -5;
-  if (ldu < plan->k) return -6;
+  if (ldu < plan->kout) return -6;
   if (!S) return -7;
   if (!V) return -8;
-  if (ldv < plan->k) return -9;
+  if (ldv < plan->kout) return -9;
   if (!piv) return -10;
   if (!workspace || ((uintptr_t)workspace & 255u)) return -11;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1139,12 +1184,22 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   plan->evset = (int)(plan->runs & 1);
   ++plan->runs;
   int rc;
-  if (plan->elem == 8)
+  if (plan->kout < plan->k) {
+    // depth l > k: the pipeline runs at depth l into the workspace, and the
+    // leading k singular triplets (S is descending) are copied out
+    if (plan->elem == 8)
+      rc = run_truncated<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S, (double *)V,
+                                 ldv, piv, ws, st, info);
+    else
+      rc = run_truncated<float>(plan, (const float *)A, lda, seed, (float *)U, ldu, (float *)S, (float *)V, ldv,
+                                piv, ws, st, info);
+  } else if (plan->elem == 8) {
     rc = run_impl<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S, (double *)V,
                           ldv, piv, ws, st, info);
-  else
+  } else {
     rc = run_impl<float>(plan, (const float *)A, lda, seed, (float *)U, ldu, (float *)S, (float *)V, ldv,
                          piv, ws, st, info);
+  }
   plan->launches = g_launches;
   return rc;
 }
@@ -1216,11 +1271,16 @@ int ffq_gemm_nt(ffsrqr_plan_t P, int64_t m, int64_t n, int r, const void *U, int
 
 extern "C" {
 
+int ffsrqr_plan_depth(ffsrqr_plan_t plan) {
+  if (!plan) return -1;
+  return plan->k;
+}
+
 int ffsrqr_plan_shape(ffsrqr_plan_t plan, int64_t *m, int64_t *n, int32_t *k, int32_t *p, int32_t *mode) {
   if (!plan) return -1;
   if (m) *m = plan->m;
   if (n) *n = plan->n;
-  if (k) *k = plan->k;
+  if (k) *k = plan->kout;
   if (p) *p = plan->p;
   if (mode) *mode = plan->mode;
   return 0;

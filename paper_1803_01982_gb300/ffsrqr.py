@@ -91,6 +91,11 @@ def _load():
     lib.ffsrqr_plan.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, ctypes.POINTER(Opts),
                                 ctypes.POINTER(ctypes.c_size_t)]
     lib.ffsrqr_plan.restype = ctypes.c_int
+    lib.ffsrqr_plan_l.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, i32, ctypes.POINTER(Opts),
+                                  ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_plan_l.restype = ctypes.c_int
+    lib.ffsrqr_plan_depth.argtypes = [P]
+    lib.ffsrqr_plan_depth.restype = ctypes.c_int
     lib.ffsrqr_run.argtypes = [P, P, i64, u64, P, i64, P, P, i64, P, P, P, ctypes.POINTER(Info)]
     lib.ffsrqr_run.restype = ctypes.c_int
     lib.ffsrqr_destroy.argtypes = [P]
@@ -173,6 +178,8 @@ lib = _load()
 
 # The C names, re-exported unchanged.
 ffsrqr_plan = lib.ffsrqr_plan
+ffsrqr_plan_l = lib.ffsrqr_plan_l
+ffsrqr_plan_depth = lib.ffsrqr_plan_depth
 ffsrqr_run = lib.ffsrqr_run
 ffsrqr_destroy = lib.ffsrqr_destroy
 ffsrqr_status_string = lib.ffsrqr_status_string
@@ -224,20 +231,26 @@ def _check(rc: int, what: str):
 
 
 class Plan:
-    """Plan + device workspace for one (m, n, k, p, mode) shape."""
+    """Plan + device workspace for one (m, n, k, p, mode) shape; l (>= k) is
+    Alg. 9's SRQR depth (None: l = k)."""
 
     def __init__(self, m: int, n: int, k: int, p: int, mode: int = PLAIN_FP32, g: float = 2.0,
-                 max_swaps: int | None = None, flags: int = 0, device=None):
+                 max_swaps: int | None = None, flags: int = 0, device=None, l: int | None = None):
         import torch
         self.m, self.n, self.k, self.p, self.mode = m, n, k, p, mode
         self.device = torch.device("cuda" if device is None else device)
         self.dtype = torch.float64 if mode == FP64 else torch.float32
-        opts = Opts(g, 4 * k if max_swaps is None else max_swaps, flags)
+        self.l = k if l is None else l
+        opts = Opts(g, 4 * self.l if max_swaps is None else max_swaps, flags)
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         with torch.cuda.device(self.device):
-            _check(lib.ffsrqr_plan(ctypes.byref(self._h), m, n, k, p, mode, ctypes.byref(opts),
-                                   ctypes.byref(ws)), "ffsrqr_plan")
+            if l is None:
+                _check(lib.ffsrqr_plan(ctypes.byref(self._h), m, n, k, p, mode, ctypes.byref(opts),
+                                       ctypes.byref(ws)), "ffsrqr_plan")
+            else:
+                _check(lib.ffsrqr_plan_l(ctypes.byref(self._h), m, n, k, l, p, mode, ctypes.byref(opts),
+                                         ctypes.byref(ws)), "ffsrqr_plan_l")
         self.workspace_bytes = ws.value
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
                                      device=self.device)

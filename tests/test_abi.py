@@ -76,3 +76,15 @@ def test_run_and_destroy_null_plan(ff):
     assert ff.ffsrqr_run(None, None, 0, 0, None, 0, None, None, 0, None, None, None, None) == -1
     assert ff.ffsrqr_destroy(None) == -1
     assert ff.ffsrqr_philox4x32_10(None, None, 1, None) == -1
+
+
+def test_plan_l_argument_errors(ff):
+    import ctypes
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 0, 5, 4, 0, None, ctypes.byref(ws)) == -4
+    assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 6, 5, 4, 0, None, ctypes.byref(ws)) == -5
+    assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 2, 5, -1, 0, None, ctypes.byref(ws)) == -6
+    assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 2, 5, 4, 9, None, ctypes.byref(ws)) == -7
+    assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 2, 5, 4, 0, None, None) == -9
+    assert ff.ffsrqr_plan_depth(None) == -1

@@ -230,3 +230,29 @@ def test_fp64_largest_k():
     assert res == pytest.approx(oracle.residual_fro(A, ref.U, ref.S, ref.V), rel=1e-10)
     np.testing.assert_allclose(got["U"].T @ got["U"], np.eye(k), atol=1e-12)
     np.testing.assert_allclose(got["V"].T @ got["V"], np.eye(k), atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", [ffsrqr.PLAIN_FP32, ffsrqr.MIXED, ffsrqr.FP64])
+def test_depth_l_returns_the_leading_triplets(mode):
+    """ffsrqr_plan_l (Alg. 9 with SRQR depth l > k) returns exactly the leading
+    k triplets and the pivots of the depth-l factorisation, and matches the
+    oracle's depth-l run."""
+    m, n, k, l, p = 600, 480, 16, 21, 8
+    A = synth.decayed(m, n, 0.9 ** np.arange(min(m, n)), 1e-4, seed=7)
+    dt = torch.float64 if mode == ffsrqr.FP64 else torch.float32
+    Ad = torch.as_tensor(A, dtype=dt).cuda()
+    pl = ffsrqr.Plan(m, n, k, p, mode, l=l)
+    U, S, V, piv = pl.run(Ad, seed=0)
+    full = ffsrqr.Plan(m, n, l, p, mode)
+    Uf, Sf, Vf, pivf = full.run(Ad, seed=0)
+    torch.cuda.synchronize()
+    assert ffsrqr.ffsrqr_plan_depth(pl._h) == l
+    assert torch.equal(S, Sf[:k]) and torch.equal(U, Uf[:, :k]) and torch.equal(V, Vf[:, :k])
+    assert torch.equal(piv, pivf)
+    ref = oracle.ffsrqr(A, k, p, seed=0, l=l)
+    So = ref.S
+    Sg = S.double().cpu().numpy()
+    if mode == ffsrqr.FP64:
+        np.testing.assert_allclose(Sg, So, rtol=1e-11)
+    else:
+        assert np.all(np.abs(Sg - So) <= 2e-5 * So[0] + 1e-5 * So)

@@ -368,3 +368,24 @@ def test_argument_checks():
         oracle.ffsrqr(A, 9, 0)
     with pytest.raises(ValueError):
         oracle.ffsrqr(A, 6, 5)    # k + p > m
+
+
+def test_depth_l_ritz_values_grow_with_the_subspace():
+    """Alg. 9 with SRQR depth l > k: on the same sketch (l + p rows) and with no
+    swaps, the first k pivots of the depth-l run are the depth-k run's (greedy
+    QRCP), so span(V'_k) lies in span(V'_l) and the Ritz values of A on it can
+    only grow (Rayleigh-Ritz monotonicity), while staying below the singular
+    values of A (interlacing)."""
+    A = synth.decayed(200, 160, 0.9 ** np.arange(160), 1e-3, seed=21, dtype=np.float64)
+    k, l, p = 8, 14, 6
+    rk = oracle.ffsrqr(A, k, p + l - k, seed=0)  # the depth-l run's sketch
+    rl = oracle.ffsrqr(A, k, p, seed=0, l=l)
+    full = oracle.ffsrqr(A, l, p, seed=0)
+    assert rk.swaps == 0 and full.swaps == 0
+    assert list(full.piv[:k]) == list(rk.piv[:k])
+    sa = np.linalg.svd(A, compute_uv=False)[:k]
+    assert np.all(rk.S <= rl.S * (1 + 1e-12)) and np.all(rl.S <= sa * (1 + 1e-12))
+    assert np.any(rl.S > rk.S * (1 + 1e-6))
+    # the depth-l result is the leading k triplets of the depth-l factorisation
+    assert np.array_equal(rl.S, full.S[:k]) and np.array_equal(rl.U, full.U[:, :k])
+    assert np.allclose(A @ rl.V, rl.U * rl.S, atol=1e-10)
