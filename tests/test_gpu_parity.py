@@ -254,5 +254,8 @@ def test_depth_l_returns_the_leading_triplets(mode):
     Sg = S.double().cpu().numpy()
     if mode == ffsrqr.FP64:
         np.testing.assert_allclose(Sg, So, rtol=1e-11)
-    else:
+    elif mode == ffsrqr.PLAIN_FP32:
         assert np.all(np.abs(Sg - So) <= 2e-5 * So[0] + 1e-5 * So)
+    else:  # the TF32 sketch may pick other pivots: the smooth-input bound of the mixed mode
+        head = So >= 0.1 * So[0]
+        assert np.all(np.abs(Sg - So)[head] <= 1e-3 * So[head])
