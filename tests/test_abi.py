@@ -88,3 +88,50 @@ def test_plan_l_argument_errors(ff):
     assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 2, 5, 4, 9, None, ctypes.byref(ws)) == -7
     assert ff.ffsrqr_plan_l(ctypes.byref(h), 100, 80, 2, 5, 4, 0, None, None) == -9
     assert ff.ffsrqr_plan_depth(None) == -1
+
+
+def test_tucker_plan_argument_errors(ff):
+    """Argument checks of ffsrqr_tucker_plan, all before any device call."""
+    import ctypes
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    dims = (ctypes.c_int64 * 3)(10, 9, 8)
+    ranks = (ctypes.c_int32 * 3)(2, 2, 2)
+    plan = ff.ffsrqr_tucker_plan
+    assert plan(None, 0, 3, dims, ranks, None, 2, 0, None, ctypes.byref(ws)) == -1
+    assert plan(ctypes.byref(h), 2, 3, dims, ranks, None, 2, 0, None, ctypes.byref(ws)) == -2
+    assert plan(ctypes.byref(h), 0, 1, dims, ranks, None, 2, 0, None, ctypes.byref(ws)) == -3
+    assert plan(ctypes.byref(h), 0, 9, dims, ranks, None, 2, 0, None, ctypes.byref(ws)) == -3
+    bad_dims = (ctypes.c_int64 * 3)(10, 0, 8)
+    assert plan(ctypes.byref(h), 0, 3, bad_dims, ranks, None, 2, 0, None, ctypes.byref(ws)) == -4
+    big = (ctypes.c_int32 * 3)(2, 10, 2)
+    assert plan(ctypes.byref(h), 0, 3, dims, big, None, 2, 0, None, ctypes.byref(ws)) == -5
+    bad_order = (ctypes.c_int32 * 3)(0, 0, 1)
+    assert plan(ctypes.byref(h), 0, 3, dims, ranks, bad_order, 2, 0, None, ctypes.byref(ws)) == -6
+    assert plan(ctypes.byref(h), 0, 3, dims, ranks, None, -1, 0, None, ctypes.byref(ws)) == -7
+    assert plan(ctypes.byref(h), 0, 3, dims, ranks, None, 2, 5, None, ctypes.byref(ws)) == -8
+    assert plan(ctypes.byref(h), 0, 3, dims, ranks, None, 2, 0, None, None) == -10
+    # k_r + p > m_j: the first step's ffsrqr_plan rejects it before any device call
+    assert plan(ctypes.byref(h), 0, 3, dims, ranks, None, 9, 0, None, ctypes.byref(ws)) == -11
+    assert plan(ctypes.byref(h), 1, 3, dims, ranks, None, 9, 0, None, ctypes.byref(ws)) == -11
+    assert ff.ffsrqr_tucker_run(None, None, 0, None, None, None, None, None, None) == -1
+    assert ff.ffsrqr_tucker_destroy(None) == -1
+    assert ff.ffsrqr_tucker_launch_count(None) == -1
+
+
+def test_rpca_argument_errors(ff):
+    import ctypes
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    create = ff.ffsrqr_rpca_create
+    assert create(None, 10, 10, None, ctypes.byref(ws)) == -1
+    assert create(ctypes.byref(h), 1, 10, None, ctypes.byref(ws)) == -2
+    assert create(ctypes.byref(h), 10, 1, None, ctypes.byref(ws)) == -3
+    assert create(ctypes.byref(h), 10, 10, None, None) == -5
+    bad_mode = ff.RpcaOpts(2, 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, 0.0)
+    assert create(ctypes.byref(h), 10, 10, ctypes.byref(bad_mode), ctypes.byref(ws)) == -4
+    neg = ff.RpcaOpts(0, 0, 0, 0, 0, 0, 0.0, 0.0, 0.0, -1.0)
+    assert create(ctypes.byref(h), 10, 10, ctypes.byref(neg), ctypes.byref(ws)) == -4
+    assert ff.ffsrqr_rpca_run(None, None, 0, None, 0, None, 0, 0, None, None, None) == -1
+    assert ff.ffsrqr_rpca_destroy(None) == -1
+    assert ff.ffsrqr_rpca_launch_count(None) == -1
