@@ -16,7 +16,7 @@
  *   Alg. 2  (TRQRCP, block size b = k)          -> oracle_srqr, first half
  *   Alg. 4  (SRQR test and swap loop)           -> oracle_srqr, second half
  *   Alg. 9  (Flip-Flop SRQR)                    -> oracle_ffsrqr
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - one TRQRCP block (b = k), SRQR depth l = k;
  *   - the trailing-norm estimate of Alg. 4 uses the updated sample
  *     B2 - B1 R11^{-1} R12 (the sample of A(l+1:m, l+1:n) that TRQRCP's

@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"):
+Tolerances (each derived from the arithmetic of the step it bounds):
   * Omega: the device evaluates Box-Muller in FP32 with CUDA's logf/sincospif,
     |z_gpu - z| <= 4e-6 (1 + |z|) against the FP64 definition; the raw Philox
     words are bit-identical.
