@@ -9,8 +9,8 @@
  *   QR of the pivoted panel A Pi(:,1:k)      (Alg. 2)
  *   (R11 R12) = Q1^T A Pi                    (Eq. RRQR)
  *   SRQR test / swaps on R11^{-1}R12 and the trailing norms (Alg. 4)
- *   QR of (R11 R12)^T -> Qhat1              (Alg. 9, line 2)
- *   tmp = A Pi Qhat1, svd(tmp) -> U, S, V    (Alg. 9, lines 3-5)
+ *   QR of (R11 R12)^T -> Qhat1              (Alg. 9)
+ *   tmp = A Pi Qhat1, svd(tmp) -> U, S, V    (Alg. 9)
  * All entry points take plain pointers and sizes; no C++ or framework types.
  *
  * Conventions

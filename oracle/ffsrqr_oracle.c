@@ -669,7 +669,7 @@ int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k,
     free(Om);
     if (trace && trace->B) memcpy(trace->B, B, sizeof(double) * (size_t)(s * n));
 
-    /* Alg. 9, line 1: SRQR to l = k steps */
+    /* Alg. 9: SRQR to l = k steps */
     double *Q1 = (double *)malloc(sizeof(double) * (size_t)(m * k));
     double *R = (double *)malloc(sizeof(double) * (size_t)(k * n));
     oracle_srqr_info si;
@@ -686,7 +686,7 @@ int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k,
     if (trace && trace->R) memcpy(trace->R, R, sizeof(double) * (size_t)(k * n));
     free(Q1);
 
-    /* Alg. 9, line 2: QRNP of (R11 R12)^T -> Qhat1 (n x k) */
+    /* Alg. 9: QRNP of (R11 R12)^T -> Qhat1 (n x k) */
     double *Rt = (double *)malloc(sizeof(double) * (size_t)(n * k));
     for (int64_t j = 0; j < k; ++j)
         for (int64_t i = 0; i < n; ++i) Rt[i * k + j] = R[j * n + i];
@@ -704,7 +704,7 @@ int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k,
     free(Qh);
     if (trace && trace->Vp) memcpy(trace->Vp, Vp, sizeof(double) * (size_t)(n * k));
 
-    /* Alg. 9, line 3: tmp = A Pi Qhat1 (m x k) */
+    /* Alg. 9: tmp = A Pi Qhat1 (m x k) */
     double *T = (double *)malloc(sizeof(double) * (size_t)(m * k));
 #pragma omp parallel for schedule(static)
     for (int64_t t = 0; t < m; ++t) {
@@ -717,7 +717,7 @@ int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k,
     }
     if (trace && trace->tmp) memcpy(trace->tmp, T, sizeof(double) * (size_t)(m * k));
 
-    /* Alg. 9, lines 4-5: svd(tmp) via Householder QR + Jacobi on R_t */
+    /* Alg. 9: svd(tmp) via Householder QR + Jacobi on R_t */
     double *Qt = (double *)malloc(sizeof(double) * (size_t)(m * k));
     double *Rtt = (double *)malloc(sizeof(double) * (size_t)(k * k));
     oracle_house_qr(T, m, k, k, Qt, Rtt);

@@ -10,11 +10,11 @@
 //   a6  R11 = triu(G(:, J)); Z^T = G^T R11^{-T}; trailing-norm estimate
 //       r_i = ||B(:,i) - B_J Z(:,i)||^2 / s; candidate c; alpha; g2  (Alg. 4)
 //   a7  swap loop while g2 > g (Alg. 4)                         [srqr_swap.cuh]
-//   a8  V' = orth(Z^T) = Pi Qhat1 up to a k x k rotation         (Alg. 9, line 2)
+//   a8  V' = orth(Z^T) = Pi Qhat1 up to a k x k rotation         (Alg. 9)
 //   a9  tmp = A V'                                               pass 3 over A
 //   a10 Y_t = tmp (R11 R_z^T)^{-1}; CholeskyQR2(Y_t) -> Q_t, R_t;
-//       M_t = R_t R11 R_z^T (tmp = Q_t M_t); Jacobi SVD of M_t   (Alg. 9, line 4)
-//   a11 U = Q_t U_s, V = V' V_s, sign rule                       (Alg. 9, line 5)
+//       M_t = R_t R11 R_z^T (tmp = Q_t M_t); Jacobi SVD of M_t   (Alg. 9)
+//   a11 U = Q_t U_s, V = V' V_s, sign rule                       (Alg. 9)
 // The thin QR factorisations are preconditioned Cholesky-QR: each tall matrix
 // is first multiplied by the inverse of a triangular factor that makes it
 // well conditioned (the sketch's R factor S11 for the panel, R11 for G^T, and

@@ -1,4 +1,4 @@
-// jacobi.cuh -- SVD of the small k x k factor M of tmp (Alg. 9, lines 4-5) by
+// jacobi.cuh -- SVD of the small k x k factor M of tmp (Alg. 9) by
 // one-sided (Hestenes) Jacobi, preconditioned by a QR factorisation, on a
 // thread-block cluster.
 //
