@@ -100,6 +100,38 @@ def oracle_sample(a, reps=1):
     return times, scale
 
 
+def tucker_cpu_baseline(X_host, ranks, st_method: bool):
+    """The FP64 oracle's Tucker decomposition of the same tensor on the host
+    cores: (seconds, sample text).  Only the benchmark calls it."""
+    import oracle
+    from oracle import tucker as otk
+    oracle.build()
+    t0 = time.perf_counter()
+    if st_method:
+        otk.sthosvd(X_host, ranks, None, p=5)
+    else:
+        otk.hosvd(X_host, ranks, p=5)
+    return time.perf_counter() - t0, "FP64 oracle on the same tensor, whole decomposition"
+
+
+def rpca_cpu_baseline(m_full: int):
+    """The FP64 oracle's IALM solve (Alg. 9 as the SVD) of a 1000 x 1000 matrix
+    of the same recipe, scaled to m_full x m_full by m n rank (the passes over
+    the matrix at the rank it converges to): (seconds at m_full, sample text)."""
+    import oracle
+    from oracle import rpca as orp
+    from paper_1803_01982_gb300 import synth
+    oracle.build()
+    ms = min(1000, m_full)
+    M, _, _ = synth.rpca_problem(ms, ms, ms // 10, int(0.05 * ms * ms), seed=1)
+    t0 = time.perf_counter()
+    orp.rpca(M, kmax=224, tol=1e-6)
+    dt = time.perf_counter() - t0
+    scale = (m_full / ms) ** 3
+    return dt * scale, (f"FP64 oracle IALM solve of the {ms}x{ms} matrix of the same recipe (tol 1e-6), "
+                        f"time scaled by m n rank to {m_full}x{m_full}")
+
+
 def cores_used():
     env = os.environ.get("OMP_NUM_THREADS")
     return int(env) if env else (os.cpu_count() or 1)
@@ -451,6 +483,10 @@ def run_tucker(a):
         roof = 3 * 12.0 * 400 * 160000 + 4.0 * 400 * (160000 + 16000 + 1600)  # + one read per core product
         name = "HOSVD (Alg. 5, factors and core) of a 400^3 FP32 tensor to ranks (40, 40, 40), p = 5"
     extra = {"gpu_launches": t.launch_count() * a.steps, "statuses": [i["status"] for i in t.infos()]}
+    if not a.no_cpu:
+        secs, sample = tucker_cpu_baseline(X.double().cpu().numpy(), ranks, st_method)
+        extra["cpu_baseline"] = {"value": 1.0 / secs, "unit": "decompositions/s", "cores": cores_used(),
+                                 "kind": "oracle", "sample": sample, "sample_seconds": secs}
     _batch_line(a, f"{name}, {a.mode}", 1, ms, roof, extra)
 
 
@@ -499,6 +535,10 @@ def run_rpca(a):
                          "frac": roof / (ms * 1e-3) / 1e9 / peaks()[0]},
             "paper_context": {"1000": "IALM_FFSRQR 1.02 s, 25 iterations, error 2.79e-7 (CPU, Sec. 4.3.1)",
                               "2000": "IALM_FFSRQR 6.93 s, 25 iterations, error 1.82e-7 (CPU, Sec. 4.3.1)"}}
+    if not a.no_cpu:
+        secs, sample = rpca_cpu_baseline(m)
+        line["cpu_baseline"] = {"value": 1.0 / secs, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+                                "sample": sample, "seconds_at_full_size": secs}
     print(json.dumps(line), flush=True)
 
 
