@@ -482,7 +482,8 @@ def run_tucker(a):
     else:
         roof = 3 * 12.0 * 400 * 160000 + 4.0 * 400 * (160000 + 16000 + 1600)  # + one read per core product
         name = "HOSVD (Alg. 5, factors and core) of a 400^3 FP32 tensor to ranks (40, 40, 40), p = 5"
-    extra = {"gpu_launches": t.launch_count() * a.steps, "statuses": [i["status"] for i in t.infos()]}
+    extra = {"metric": "Tucker decompositions/s", "unit": "decompositions/s",
+             "gpu_launches": t.launch_count() * a.steps, "statuses": [i["status"] for i in t.infos()]}
     if not a.no_cpu:
         secs, sample = tucker_cpu_baseline(X.double().cpu().numpy(), ranks, st_method)
         extra["cpu_baseline"] = {"value": 1.0 / secs, "unit": "decompositions/s", "cores": cores_used(),
