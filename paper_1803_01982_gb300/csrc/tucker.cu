@@ -1,4 +1,4 @@
-// sthosvd.cu -- Tucker approximations of dense tensors (Sec. 3.1) with
+// tucker.cu -- Tucker approximations of dense tensors (Sec. 3.1) with
 // Flip-Flop SRQR (Alg. 9) as the approximate rank-k_r SVD of each unfolding:
 // the sequentially truncated HOSVD (Alg. 6) and the HOSVD (Alg. 5).
 //
