@@ -58,12 +58,14 @@ def parse():
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batch", "hosvd", "sthosvd", "hosvd-core", "rpca", "serving"],
+    ap.add_argument("--workload", choices=["single", "batch", "hosvd", "sthosvd", "hosvd-core", "rpca", "rsisvd",
+                                           "serving"],
                     default="single",
                     help="single: one 20000x20000 problem (default); batch: 256 uneven matrices in one graph; "
                          "hosvd: the three unfoldings of a 400^3 tensor; sthosvd: sequentially truncated HOSVD "
                          "of that tensor; hosvd-core: its HOSVD with the core; rpca: IALM robust PCA of an "
-                         "--m x --m matrix; serving: Poisson request stream")
+                         "--m x --m matrix; rsisvd: randomized subspace iteration against FFSRQR on the default "
+                         "matrix; serving: Poisson request stream")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     return ap.parse_args()
@@ -543,6 +545,54 @@ def run_rpca(a):
     print(json.dumps(line), flush=True)
 
 
+def run_rsisvd(a):
+    """Randomized subspace iteration (the paper's appendix algorithm; p = 5,
+    q = 1, its parameters in Sec. 4.1) against Flip-Flop SRQR on the default
+    workload (20000 x 20000, sigma_j = j^-1.5, k = 200), both on this library's
+    kernels in --mode.  One step = one approximation.  The accuracy of both is
+    measured after the timed region as ||A - U S V^T||_F / ||A||_F (a torch
+    product, verification only)."""
+    import torch
+
+    from paper_1803_01982_gb300 import ffsrqr, synth
+    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    r = min(2000, a.m, a.n)
+    A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=1)
+    st = torch.cuda.current_stream()
+    res = {}
+    for name, plan in (("rsisvd", ffsrqr.Plan(a.m, a.n, a.k, 5, mode, rsi_q=1)),
+                       ("ffsrqr", ffsrqr.Plan(a.m, a.n, a.k, a.p, mode))):
+        out = plan.outputs()
+        for _ in range(a.warmup):
+            plan.run(A, 0, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(a.steps):
+            plan.run(A, 0, out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        U, S, V, _ = out
+        err = float(torch.linalg.norm(A - (U * S) @ V.T) / torch.linalg.norm(A))
+        res[name] = {"ms": e0.elapsed_time(e1) / a.steps, "rel_error_fro": err,
+                     "launches": ffsrqr.ffsrqr_launch_count(plan._h), "status": plan.info()["status"],
+                     "sigma_1": float(S[0]), "sigma_k": float(S[-1])}
+    ms = res["rsisvd"]["ms"]
+    peak, src = peaks()
+    roof_bytes = 4.0 * a.m * a.n * 4  # q = 1: four reads of A
+    line = {"metric": METRIC, "value": 1000.0 / ms, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"RSISVD (p = 5, q = 1) of {a.m}x{a.n} FP32, r=2000, "
+                                   f"{'sigma_j=j^-1.5' if a.decay == 'slow' else 'sigma_j=0.97^j'}, k={a.k}, "
+                                   f"{a.mode}"},
+            "roofline": {"bound": "hbm", "achieved": roof_bytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": roof_bytes / (peak * 1e9) / (ms * 1e-3), "peak_source": src,
+                         "algorithmic_bytes_per_step": roof_bytes, "note": "four reads of A"},
+            "gpu_launches": res["rsisvd"]["launches"] * a.steps, "comparison": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(a):
     """Poisson arrivals (mean a.rate per second, a.duration seconds) of
     truncated-SVD requests like singular-value-thresholding iterates:
@@ -613,7 +663,7 @@ def main():
     a = parse()
     if a.workload != "single" and a.impl == "ours":
         {"batch": run_batch, "hosvd": run_hosvd, "sthosvd": run_tucker, "hosvd-core": run_tucker,
-         "rpca": run_rpca, "serving": run_serving}[a.workload](a)
+         "rpca": run_rpca, "rsisvd": run_rsisvd, "serving": run_serving}[a.workload](a)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -111,6 +111,20 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
 int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t l, int32_t p, int32_t mode,
                   const ffsrqr_opts_t *opts, size_t *workspace_bytes);
 
+/* A plan that ffsrqr_run executes as approximate SVD by randomized subspace
+ * iteration (the paper's appendix algorithm, the method Sec. 3.2 compares
+ * against) with l = k + p columns and q iterations, on the same kernels:
+ * Omega (n x l, Philox stream 0, element (i, j) = draw i l + j), Q = orth(A
+ * Omega); q times V' = orth(A^T Q), Q = orth(A V'); then A^T Q = V' R,
+ * svd(R^T) = W S Z^T, U = Q W, V = V' Z, the leading k triplets (sign rule as
+ * Alg. 9).  orth() is CholeskyQR2, exact in exact arithmetic for any full-rank
+ * input and reliable in FP32 up to cond(A Omega) of about 1e4.  piv is not
+ * written.  Requirements: 1 <= k, k + p <= min(m, n), q >= 0, k + p <= 224
+ * (FP32) / 160 (FP64).  Errors: -1 plan NULL, -2 m, -3 n, -4 k, -5 p, -6 q,
+ * -7 mode, -8 opts, -9 workspace_bytes NULL, and ffsrqr_plan's statuses. */
+int ffsrqr_plan_rsi(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t q, int32_t mode,
+                    const ffsrqr_opts_t *opts, size_t *workspace_bytes);
+
 /* SRQR depth l of a plan (k for plans made by ffsrqr_plan); -1 for NULL. */
 int ffsrqr_plan_depth(ffsrqr_plan_t plan);
 

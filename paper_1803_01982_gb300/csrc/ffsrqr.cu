@@ -83,6 +83,7 @@ struct ffsrqr_plan_s {
   int64_t m, n;
   int k, p, s, mode;
   int kout;                       // rank returned (Alg. 9's k); k above is the SRQR depth l >= kout
+  int rsi_q;                      // >= 0: the plan runs randomized subspace iteration with q iterations
   size_t off_uo, off_so, off_vo;  // l > kout: the depth-l U, S, V before truncation
   double g;
   int max_swaps, flags;
@@ -887,6 +888,113 @@ int run_truncated(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U
   return 0;
 }
 
+// Approximate SVD by randomized subspace iteration (the paper's appendix
+// algorithm) on this plan's kernels, with l = P->k = kout + p columns:
+//   Omega (n x l);  Q = orth(A Omega);  q times: V' = orth(A^T Q), Q = orth(A V');
+//   A^T Q = V' R_z  (so Q^T A = R_z^T V'^T);  svd(R_z^T) = W S Z^T;
+//   U = Q W, V = V' Z, the leading kout triplets.
+// orth() is CholeskyQR2; the passes and products are the Flip-Flop SRQR ones.
+template <typename T>
+int run_rsi(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
+            int64_t ldv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
+  const int64_t m = P->m, n = P->n, ldk = P->ldk;
+  const int l = P->k, k = P->kout, nsm = P->num_sms;
+  WsPtrs<T> w = ws_ptrs<T>(P, ws);
+  int rc;
+  CK(cudaMemsetAsync(ws + P->off_ctl, 0, CTL_WORDS * sizeof(int), st));
+  CK(cudaMemsetAsync(ws + P->off_dctl, 0, D_WORDS * sizeof(double), st));
+  init_ctl_kernel<<<1, 32, 0, st>>>(w.ctl, w.dctl);
+  CKL("init_ctl");
+  // Omega, n x l row-major (element (i, j) is draw i l + j), into V'
+  {
+    const int64_t nq = cdiv(n * l, 4);
+    omega_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(nq, 256), 8 * nsm), 256, 0, st>>>(w.vp, (int)n, l, ldk,
+                                                                                         seed);
+    CKL("omega");
+  }
+  const bool tc = use_tc<T>(P, A, lda);
+  auto right = [&](const T *X, T *C) -> int {  // C (m x l) = A X, X n x l
+    if (tc) return tc_thin_pass(st, P, ws, false, (const float *)A, lda, (const float *)X, n, (float *)C);
+    return launch_gemm<T>(st, P, ws, (int)m, l, (int)n, A, lda, false, X, ldk, true, C, ldk);
+  };
+  auto left = [&](const T *X, T *C) -> int {  // C (n x l) = A^T X, X m x l
+    if (tc) return tc_thin_pass(st, P, ws, true, (const float *)A, lda, (const float *)X, m, (float *)C);
+    return launch_gemm<T>(st, P, ws, (int)n, l, (int)m, A, lda, true, X, ldk, true, C, ldk);
+  };
+  auto orth = [&](const T *X, int64_t rows, T *Q, T *R) -> int {  // Q = X R^{-1}
+    if (tc) return cholqr2_tc(st, P, ws, (const float *)X, rows, (float *)Q, (float *)R);
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(rows * l, 256), 8 * nsm), 256, 0, st>>>(X, ldk, Q, ldk,
+                                                                                               rows, l, nullptr);
+    CKL("copy_orth");
+    return cholqr2<T>(st, P, ws, Q, ldk, rows, R);
+  };
+  if ((rc = right(w.vp, w.tmp)) || (rc = orth(w.tmp, m, w.yt, nullptr))) return rc;
+  for (int it = 0; it < P->rsi_q; ++it) {
+    if ((rc = left(w.yt, w.gt)) || (rc = orth(w.gt, n, w.vp, nullptr))) return rc;
+    if ((rc = right(w.vp, w.tmp)) || (rc = orth(w.tmp, m, w.yt, nullptr))) return rc;
+  }
+  if ((rc = left(w.yt, w.gt)) || (rc = orth(w.gt, n, w.vp, w.rz))) return rc;
+  // M = R_z^T (l x l): Q^T A = M V'^T
+  transpose_kernel<T><<<dim3((unsigned)cdiv(l, 32), (unsigned)cdiv(l, 32)), dim3(32, 8), 0, st>>>(w.rz, l, l, l,
+                                                                                                  w.mt, l);
+  CKL("transpose_rz");
+  // outputs at full width l: to the caller's buffers when kout = l
+  T *uo = (k < l) ? reinterpret_cast<T *>(ws + P->off_uo) : U;
+  T *so = (k < l) ? reinterpret_cast<T *>(ws + P->off_so) : S;
+  T *vo = (k < l) ? reinterpret_cast<T *>(ws + P->off_vo) : V;
+  const int64_t lduo = (k < l) ? l : ldu, ldvo = (k < l) ? l : ldv;
+  {
+    // the small SVD of the Flip-Flop SRQR pipeline: QR of M^T, Jacobi on R^T,
+    // Q of the small QR formed on the side stream
+    const size_t qsmem = precond_qr_smem(l, sizeof(T));
+    precond_qr_r_kernel<T><<<1, 1024, qsmem, st>>>(w.mt, l, w.t1, w.qv);
+    CKL("precond_qr_r");
+    CK(cudaEventRecord(P->ev_fork, st));
+    CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    precond_qr_q_kernel<T><<<1, 1024, qsmem, P->side>>>(l, w.qv, w.qg);
+    CKL("precond_qr_q");
+    CK(cudaEventRecord(P->ev_join, P->side));
+    const T eps = (sizeof(T) == 4) ? T(5.9604645e-8) : T(1.1102230246251565e-16);
+    const T tol = (sizeof(T) == 4) ? T(4) * sqrt(T(l)) * eps : T(l) * eps;
+    if ((rc = launch_jacobi<T>(st, P, w.t1, (const T *)nullptr, w.us, so, w.t1, w.ctl, tol))) return rc;
+    CK(cudaStreamWaitEvent(st, P->ev_join, 0));
+    if ((rc = launch_gemm<T>(st, P, ws, l, l, l, w.qg, l, true, w.t1, l, true, w.vs, l))) return rc;
+  }
+  if (tc) {
+    const TcBufs tb = tc_bufs(P, ws);
+    if ((rc = tc_split_t(st, (const float *)w.us, l, l, l, tb.sh, tb.sl, ldk))) return rc;
+    if ((rc = tc_mul(st, P, ws, (const float *)w.yt, ldk, m, l, l, (float *)uo, lduo))) return rc;
+    if ((rc = tc_split_t(st, (const float *)w.vs, l, l, l, tb.sh, tb.sl, ldk))) return rc;
+    if ((rc = tc_mul(st, P, ws, (const float *)w.vp, ldk, n, l, l, (float *)vo, ldvo))) return rc;
+  } else {
+    if ((rc = launch_gemm<T>(st, P, ws, (int)m, l, l, w.yt, ldk, false, w.us, l, true, uo, lduo))) return rc;
+    if ((rc = launch_gemm<T>(st, P, ws, (int)n, l, l, w.vp, ldk, false, w.vs, l, true, vo, ldvo))) return rc;
+  }
+  sign_partial_kernel<T><<<P->nblk_sign, 256, 0, st>>>(uo, lduo, m, l, w.sgnv, w.sgni);
+  CKL("sign_partial");
+  sign_final_kernel<T><<<(unsigned)cdiv(l, 256), 256, 0, st>>>(uo, lduo, l, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
+  CKL("sign_final");
+  scale_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * l, 256), 8 * nsm), 256, 0, st>>>(uo, lduo, m, l,
+                                                                                              w.sgn);
+  scale_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * l, 256), 8 * nsm), 256, 0, st>>>(vo, ldvo, n, l,
+                                                                                              w.sgn);
+  CKL("scale_cols");
+  if (k < l) {
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(uo, l, U, ldu, m, k,
+                                                                                            nullptr);
+    CKL("copy_u");
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(vo, l, V, ldv, n, k,
+                                                                                            nullptr);
+    CKL("copy_v");
+    CK(cudaMemcpyAsync(S, so, (size_t)k * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+  ffsrqr_info_t *dinfo = reinterpret_cast<ffsrqr_info_t *>(ws + P->off_info);
+  info_kernel<<<1, 32, 0, st>>>(w.ctl, w.dctl, dinfo);
+  CKL("info");
+  if (info) CK(cudaMemcpyAsync(info, dinfo, sizeof(ffsrqr_info_t), cudaMemcpyDeviceToHost, st));
+  return 0;
+}
+
 template <typename T>
 void layout(ffsrqr_plan_s *P) {
   const int64_t m = P->m, n = P->n;
@@ -1114,6 +1222,7 @@ int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32
   P->n = n;
   P->k = k;
   P->kout = kout;
+  P->rsi_q = -1;  // Flip-Flop SRQR unless ffsrqr_plan_rsi says otherwise
   P->p = p;
   P->s = k + p;
   P->mode = mode;
@@ -1184,7 +1293,14 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   plan->evset = (int)(plan->runs & 1);
   ++plan->runs;
   int rc;
-  if (plan->kout < plan->k) {
+  if (plan->rsi_q >= 0) {
+    if (plan->elem == 8)
+      rc = run_rsi<double>(plan, (const double *)A, lda, seed, (double *)U, ldu, (double *)S, (double *)V, ldv, ws,
+                           st, info);
+    else
+      rc = run_rsi<float>(plan, (const float *)A, lda, seed, (float *)U, ldu, (float *)S, (float *)V, ldv, ws, st,
+                          info);
+  } else if (plan->kout < plan->k) {
     // depth l > k: the pipeline runs at depth l into the workspace, and the
     // leading k singular triplets (S is descending) are copied out
     if (plan->elem == 8)
@@ -1270,6 +1386,27 @@ int ffq_gemm_nt(ffsrqr_plan_t P, int64_t m, int64_t n, int r, const void *U, int
 }
 
 extern "C" {
+
+int ffsrqr_plan_rsi(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t q, int32_t mode,
+                    const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (m < 1 || m > (int64_t)INT32_MAX) return -2;
+  if (n < 1 || n > (int64_t)INT32_MAX) return -3;
+  if (k < 1 || k > n || k > m) return -4;
+  if (p < 0 || (int64_t)k + p > std::min(m, n)) return -5;
+  if (q < 0) return -6;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -7;
+  if (opts && (!(opts->g > 1.0) || opts->max_swaps < 0)) return -8;
+  if (!workspace_bytes) return -9;
+  // a plan at width l = k + p (no sketch oversampling of its own) whose
+  // outputs are cut to k columns
+  const int rc = ffsrqr_plan_l(plan, m, n, k, k + p, 0, mode, opts, workspace_bytes);
+  if (rc < 0) return -5;
+  if (rc > 0) return rc;
+  (*plan)->rsi_q = q;
+  return 0;
+}
 
 int ffsrqr_plan_depth(ffsrqr_plan_t plan) {
   if (!plan) return -1;

@@ -94,6 +94,9 @@ def _load():
     lib.ffsrqr_plan_l.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, i32, ctypes.POINTER(Opts),
                                   ctypes.POINTER(ctypes.c_size_t)]
     lib.ffsrqr_plan_l.restype = ctypes.c_int
+    lib.ffsrqr_plan_rsi.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, i32, ctypes.POINTER(Opts),
+                                    ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_plan_rsi.restype = ctypes.c_int
     lib.ffsrqr_plan_depth.argtypes = [P]
     lib.ffsrqr_plan_depth.restype = ctypes.c_int
     lib.ffsrqr_run.argtypes = [P, P, i64, u64, P, i64, P, P, i64, P, P, P, ctypes.POINTER(Info)]
@@ -180,6 +183,7 @@ lib = _load()
 ffsrqr_plan = lib.ffsrqr_plan
 ffsrqr_plan_l = lib.ffsrqr_plan_l
 ffsrqr_plan_depth = lib.ffsrqr_plan_depth
+ffsrqr_plan_rsi = lib.ffsrqr_plan_rsi
 ffsrqr_run = lib.ffsrqr_run
 ffsrqr_destroy = lib.ffsrqr_destroy
 ffsrqr_status_string = lib.ffsrqr_status_string
@@ -232,10 +236,12 @@ def _check(rc: int, what: str):
 
 class Plan:
     """Plan + device workspace for one (m, n, k, p, mode) shape; l (>= k) is
-    Alg. 9's SRQR depth (None: l = k)."""
+    Alg. 9's SRQR depth (None: l = k).  rsi_q (not None): the plan runs
+    randomized subspace iteration with that many iterations instead."""
 
     def __init__(self, m: int, n: int, k: int, p: int, mode: int = PLAIN_FP32, g: float = 2.0,
-                 max_swaps: int | None = None, flags: int = 0, device=None, l: int | None = None):
+                 max_swaps: int | None = None, flags: int = 0, device=None, l: int | None = None,
+                 rsi_q: int | None = None):
         import torch
         self.m, self.n, self.k, self.p, self.mode = m, n, k, p, mode
         self.device = torch.device("cuda" if device is None else device)
@@ -245,7 +251,10 @@ class Plan:
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         with torch.cuda.device(self.device):
-            if l is None:
+            if rsi_q is not None:  # randomized subspace iteration with rsi_q iterations
+                _check(lib.ffsrqr_plan_rsi(ctypes.byref(self._h), m, n, k, p, rsi_q, mode, ctypes.byref(opts),
+                                           ctypes.byref(ws)), "ffsrqr_plan_rsi")
+            elif l is None:
                 _check(lib.ffsrqr_plan(ctypes.byref(self._h), m, n, k, p, mode, ctypes.byref(opts),
                                        ctypes.byref(ws)), "ffsrqr_plan")
             else:

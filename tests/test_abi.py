@@ -135,3 +135,18 @@ def test_rpca_argument_errors(ff):
     assert ff.ffsrqr_rpca_run(None, None, 0, None, 0, None, 0, 0, None, None, None) == -1
     assert ff.ffsrqr_rpca_destroy(None) == -1
     assert ff.ffsrqr_rpca_launch_count(None) == -1
+
+
+def test_plan_rsi_argument_errors(ff):
+    import ctypes
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    f = ff.ffsrqr_plan_rsi
+    assert f(None, 100, 80, 5, 5, 1, 0, None, ctypes.byref(ws)) == -1
+    assert f(ctypes.byref(h), 0, 80, 5, 5, 1, 0, None, ctypes.byref(ws)) == -2
+    assert f(ctypes.byref(h), 100, 0, 5, 5, 1, 0, None, ctypes.byref(ws)) == -3
+    assert f(ctypes.byref(h), 100, 80, 0, 5, 1, 0, None, ctypes.byref(ws)) == -4
+    assert f(ctypes.byref(h), 100, 80, 10, 75, 1, 0, None, ctypes.byref(ws)) == -5
+    assert f(ctypes.byref(h), 100, 80, 10, 5, -1, 0, None, ctypes.byref(ws)) == -6
+    assert f(ctypes.byref(h), 100, 80, 10, 5, 1, 9, None, ctypes.byref(ws)) == -7
+    assert f(ctypes.byref(h), 100, 80, 10, 5, 1, 0, None, None) == -9
