@@ -159,6 +159,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int
   return s_ok != 0;
 }
 
+// Raise a kernel's dynamic shared-memory cap to the most the device allows for
+// it (the opt-in maximum less the kernel's static shared memory).  Every
+// caller sets this same value, so host threads that launch one kernel with
+// different sizes never lower the cap under one another's launch.
+inline cudaError_t smem_cap_max(const void *fn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 __host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 

@@ -8,19 +8,20 @@
 // cudaMalloc could fail or would have to wait for memory held elsewhere.
 // Such a caller keeps the sketch and the outputs in memory it already owns.
 //
-// The scratch is one static __device__ array (QS_BYTES, below 1 MiB); its
-// address is resolved with cudaGetSymbolAddress once per device, with that
-// device current, on the first call (so that first call does host-side set-up
-// and is best made before any stream capture).  Every call zeroes the part
-// that must start at zero (the control words: grid-barrier counter, status)
-// and the per-column selection flags with cudaMemsetAsync on its stream.
-// Because all calls on one device share the array, calls whose executions
-// overlap (on different streams without an ordering between them) race:
-// serialise them on one stream or with events.
+// The scratch is one static __device__ array (QS_BYTES, below 1 MiB) that
+// every device loading the library holds until the process exits.  In host
+// code its name only stands for it: the device address is looked up with
+// cudaGetSymbolAddress, with the calling device current, on every call (a
+// host-side lookup; the first call on a device also loads the module, so make
+// it before any stream capture).  Every call zeroes the part that must start
+// at zero (the control words: grid-barrier counter, status) and the
+// per-column selection flags with cudaMemsetAsync on its stream.  Because all
+// calls on one device share the array, calls whose executions overlap (on
+// different streams without an ordering between them) race: serialise them
+// on one stream or with events.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "../../include/ffsrqr.h"
 #include "common.cuh"
@@ -33,7 +34,6 @@ namespace {
 constexpr int64_t QS_MAX_N = 65536;  // columns of the sketch
 constexpr int64_t QS_MAX_LDS = 256;  // leading dimension of B^T (>= s)
 constexpr int QS_MAX_GRID = 256;     // blocks of the cooperative QRCP
-constexpr int QS_MAX_DEV = 64;
 constexpr size_t QS_CTL = 256;       // CTL_WORDS control words, zeroed per call
 constexpr size_t QS_CVAL = QS_CTL;
 constexpr size_t QS_CIDX = QS_CVAL + sizeof(float) * 2 * QS_MAX_GRID;
@@ -57,9 +57,6 @@ __global__ void qs_posdiag_kernel(float *__restrict__ R, int k) {
   }
 }
 
-std::mutex g_mu;
-unsigned char *g_base[QS_MAX_DEV] = {};
-
 }  // namespace
 
 extern "C" int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t lds, int32_t k,
@@ -72,20 +69,16 @@ extern "C" int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t
   if (!piv) return -6;
   if (!S11) return -7;
   if (n > QS_MAX_N || lds > QS_MAX_LDS) return FFSRQR_STATUS_UNSUPPORTED;
-  if ((size_t)k * k * sizeof(float) > 200 * 1024) return FFSRQR_STATUS_UNSUPPORTED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0, nsm = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FFSRQR_STATUS_CUDA;
-  if (dev < 0 || dev >= QS_MAX_DEV) return FFSRQR_STATUS_UNSUPPORTED;
+  // the scratch's address on the current device (never cached: a context that
+  // was reset and re-created would leave a cached address stale)
   unsigned char *base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_base[dev]) {
-      void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_qrcp_scratch) != cudaSuccess || !p) return FFSRQR_STATUS_CUDA;
-      g_base[dev] = reinterpret_cast<unsigned char *>(p);
-    }
-    base = g_base[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_qrcp_scratch) != cudaSuccess || !p) return FFSRQR_STATUS_CUDA;
+    base = reinterpret_cast<unsigned char *>(p);
   }
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -103,9 +96,7 @@ extern "C" int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t
     if (grid >= gmax) return FFSRQR_STATUS_UNSUPPORTED;
     grid = std::min<int64_t>(gmax, grid * 2);
   }
-  if (cudaFuncSetAttribute(qrcp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return FFSRQR_STATUS_CUDA;
+  if (smem_cap_max((const void *)qrcp_kernel<float>) != cudaSuccess) return FFSRQR_STATUS_CUDA;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel<float>, 512, smem) != cudaSuccess ||
       per_sm < 1)
@@ -128,6 +119,7 @@ extern "C" int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t
   qa.sel = sel;
   qa.ctl = ctl;
   qa.spin_limit = 2000000;
+  qa.stall_step = -1;
   qa.cols_per_block = cols;
   qa.s_pad = spad;
   void *args[] = {&qa};
