@@ -70,6 +70,13 @@ typedef struct {
 /* opts.flags bits */
 #define FFSRQR_FLAG_CHECK_FINITE 1 /* scan A for Inf/NaN first (one extra read of A) */
 #define FFSRQR_FLAG_PHASE_TIMES 2  /* record CUDA events between pipeline phases */
+/* Failure injection for testing the device-side failure detection: the grid
+ * barrier of the sketch QRCP's last step waits for one block more than the
+ * grid holds, so that wait expires (after about a second) and the run
+ * reports FFSRQR_STATUS_TIMEOUT; the outputs of such a run are not
+ * meaningful.  Nothing faults or hangs: every later kernel still runs to its
+ * own bounds, and the next run on the same context is unaffected. */
+#define FFSRQR_FLAG_TEST_STALL 4
 
 /* Per-run report, written by a device->host copy enqueued at the end of
  * ffsrqr_run; valid after the stream has been synchronised.
@@ -209,17 +216,26 @@ int ffsrqr_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int32_t count, 
  *          index).
  *   S11    device, k x k row-major FP32 out: the R factor of the pivoted
  *          columns, rows flipped so that its diagonal is non-negative.
- *   status device int32 out or NULL: 0, FFSRQR_STATUS_RANK_DEFICIENT (a zero
- *          trailing norm) or FFSRQR_STATUS_TIMEOUT (bounded wait expired).
- * Limits of the static scratch: n <= 65536, lds <= 256 (so s <= 256), and
- * the sketch must fit the blocks' shared memory (else
- * FFSRQR_STATUS_UNSUPPORTED).  Nothing is allocated: the scratch is resolved
- * once per device on the first call (host-side set-up; make that call first,
- * outside any stream capture) and the words that must start at zero are
- * cleared with cudaMemsetAsync on stream.  Calls on one device share the
- * scratch, so calls that may execute at the same time race: order them on
- * one stream or with events.  Enqueues only; results valid after the stream
- * is synchronised.  Returns 0, -i for an invalid i-th argument (1 Bt, 2 n,
+ *   status device int32 out or NULL: the largest of the codes met --
+ *          0; FFSRQR_STATUS_RANK_DEFICIENT (a winner with zero trailing
+ *          norm; outputs complete); FFSRQR_STATUS_TIMEOUT (a bounded grid
+ *          wait expired: piv and S11 are written only for the steps before
+ *          it); FFSRQR_STATUS_NONFINITE (no column with a finite trailing
+ *          norm was left at some step, e.g. NaN in Bt: that step and the
+ *          later ones are skipped, so piv[j] and column j of S11 keep
+ *          what the caller had there for every skipped step j, up to the
+ *          sign of each row, which the non-negative-diagonal normalisation
+ *          of the completed rows may flip).
+ * Limits of the static scratch: n <= 65536, lds <= 256 (so s <= 256 and
+ * k <= 256), and the sketch slabs must fit the blocks' shared memory (else
+ * FFSRQR_STATUS_UNSUPPORTED).  Nothing is allocated: the scratch's device
+ * address is looked up on every call with the calling device current (the
+ * first call on a device also loads the module: make it outside any stream
+ * capture), and the words that must start at zero are cleared with
+ * cudaMemsetAsync on stream.  Calls on one device share the scratch, so
+ * calls that may execute at the same time race: order them on one stream or
+ * with events.  Enqueues only; results valid after the stream is
+ * synchronised.  Returns 0, -i for an invalid i-th argument (1 Bt, 2 n,
  * 3 s, 4 lds < s, 5 k outside [1, min(s, n)], 6 piv, 7 S11),
  * FFSRQR_STATUS_UNSUPPORTED beyond the limits, FFSRQR_STATUS_CUDA on a CUDA
  * error. */

@@ -42,6 +42,7 @@ struct QrcpArgs {
   int *sel;          // [n] 1 if selected (written for downstream kernels)
   int *ctl;
   long long spin_limit;
+  int stall_step;      // failure injection: this step's barrier waits for one block too many (-1: none)
   int cols_per_block;  // slab width (columns)
   int s_pad;           // slab column stride in shared memory
 };
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
         a.cand_col[((size_t)buf * G + b) * a.lds + t] = slab[(size_t)lc * a.s_pad + t];
     }
     // 2. barrier
-    if (!grid_barrier(bar, (unsigned)((j + 1) * G), a.ctl, a.spin_limit)) return;
+    if (!grid_barrier(bar, (unsigned)((j + 1) * G + (j == a.stall_step ? 1 : 0)), a.ctl, a.spin_limit)) return;
     // 3. winner, reflector
     {
       T wv = neg_inf<T>();

@@ -324,6 +324,7 @@ PHASES = ["omega", "pass1_sketch", "qrcp", "panel_qr", "pass2_r12", "srqr_test",
           "tc_pass1_kernel", "tc_pass2_kernel", "tc_pass3_kernel"]
 FLAG_CHECK_FINITE = 1
 FLAG_PHASE_TIMES = 2
+FLAG_TEST_STALL = 4
 
 
 def phase_times(plan: "Plan", back: int = 0) -> dict:
