@@ -33,6 +33,7 @@
 #include "dense_small.cuh"
 #include "gemm_simt.cuh"
 #include "jacobi.cuh"
+#include "jacobi_blk.cuh"
 #include "philox.cuh"
 #include "qrcp.cuh"
 #include "srqr_swap.cuh"
@@ -280,7 +281,7 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
 #define TC_LAUNCH(BKv, NPv, AMNv)                                                                    \
   {                                                                                                  \
     auto fn = tc_gemm_kernel<BKv, NPv, AMNv>;                                                        \
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));            \
+    CK(smem_cap_max((const void *)fn));                                                               \
     if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[P->evset][pass][0], st);                     \
     fn<<<sc.G, TC_THREADS, smem, st>>>(mA, mB, mBl, sc);                                             \
     if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[P->evset][pass][1], st);                     \
@@ -325,14 +326,14 @@ int launch_trsm(cudaStream_t st, const ffsrqr_plan_s *P, T *X, int64_t ldx, int6
     if constexpr (sizeof(T) == 4) {                                                                    \
       if (packed) {                                                                                    \
         auto fn2 = trsm_rows2_kernel<NSv, 5, FWD>;                                                     \
-        CK(cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
+        CK(smem_cap_max((const void *)fn2));                                                            \
         fn2<<<grid, threads, smem, st>>>((float *)X, ldx, M, k, (const float *)Pm, psi, psj, gate);    \
         CKL("trsm_rows2");                                                                             \
         return 0;                                                                                      \
       }                                                                                                \
     }                                                                                                  \
     auto fn = few ? trsm_rows_kernel<T, NSv, 1, FWD> : trsm_rows_kernel<T, NSv, 4, FWD>;               \
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));              \
+    CK(smem_cap_max((const void *)fn));                                                                 \
     fn<<<grid, threads, smem, st>>>(X, ldx, M, k, Pm, psi, psj, gate);                                 \
     CKL("trsm_rows");                                                                                  \
     return 0;                                                                                          \
@@ -349,7 +350,7 @@ template <typename T>
 int launch_chol(cudaStream_t st, const ffsrqr_plan_s *P, const T *W, T *R, int *ctl) {
   const int k = P->k;
   const size_t smem = (size_t)k * k * sizeof(T);
-  CK(cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(smem_cap_max((const void *)cholesky_kernel<T>));
   cholesky_kernel<T><<<1, 512, smem, st>>>(W, k, R, ctl);
   CKL("cholesky");
   return 0;
@@ -625,6 +626,31 @@ int launch_jacobi(cudaStream_t st, const ffsrqr_plan_s *P, const T *X, const T *
   return 0;
 }
 
+// Single-precision SVD of the small factor M (kk x kk, row-major, leading
+// dimension ldm): U_s, V_s (kk x kk, row-major) and S by the column-block
+// cluster Jacobi on M^T.  query: only ask how many such clusters the device
+// can hold at once.
+cudaError_t launch_jacobi_blk(cudaStream_t st, const float *M, int kk, int ldm, float *Us, float *S, float *Vs,
+                              int *ctl, bool query = false, int *clusters = nullptr) {
+  const int C = jb_cluster_for(kk);
+  const JbGeom g = jb_geom(kk, C);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3((unsigned)(32 * g.nw));
+  cfg.dynamicSmemBytes = jb_smem_bytes(kk);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query) return cudaOccupancyMaxActiveClusters(clusters, jacobi_blk_kernel, &cfg);
+  const float tol = 4.f * sqrtf((float)kk) * 5.9604645e-8f;
+  return cudaLaunchKernelEx(&cfg, jacobi_blk_kernel, M, kk, ldm, tol, (int)JB_MAX_SWEEPS, Us, S, Vs, ctl);
+}
+
 template <typename T>
 int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
              int64_t ldv, int32_t *piv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
@@ -681,11 +707,11 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
     qa.sel = w.sel;
     qa.ctl = w.ctl;
     qa.spin_limit = kSpinLimit;
+    qa.stall_step = (P->flags & FFSRQR_FLAG_TEST_STALL) ? k - 1 : -1;
     qa.cols_per_block = P->qrcp_cols;
     qa.s_pad = P->qrcp_spad;
     void *args[] = {&qa};
-    CK(cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)P->qrcp_smem));
+    CK(smem_cap_max((const void *)qrcp_kernel<T>));
     CK(cudaLaunchCooperativeKernel((void *)qrcp_kernel<T>, dim3(P->qrcp_grid), dim3(P->qrcp_threads),
                                    args, P->qrcp_smem, st));
     ++g_launches;
@@ -771,8 +797,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
     sa.max_swaps = P->max_swaps;
     sa.spin_limit = kSpinLimit;
     void *args[] = {&sa};
-    CK(cudaFuncSetAttribute(srqr_swap_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)P->swap_smem));
+    CK(smem_cap_max((const void *)srqr_swap_kernel<T>));
     CK(cudaLaunchCooperativeKernel((void *)srqr_swap_kernel<T>, dim3(P->swap_grid), dim3(512), args,
                                    P->swap_smem, st));
     ++g_launches;
@@ -817,7 +842,11 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.rt, k, false, w.r11, k, true, w.t1, k))) return rc;
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.t1, k, false, w.rz, k, false, w.mt, k))) return rc;
   MARK(10);
-  {
+  if constexpr (sizeof(T) == 4) {
+    // single precision: column-block cluster Jacobi on M_t^T
+    CK(launch_jacobi_blk(st, (const float *)w.mt, k, k, (float *)w.us, (float *)S, (float *)w.vs, w.ctl));
+    ++g_launches;
+  } else {
     // M_t^T = Q R: X = R^T to t1 and the reflectors to qv; Q (to qg) is formed
     // on the plan's side stream while the cluster Jacobi runs on [X; I]; then
     // V_s = Q J (J to t1, which the Jacobi no longer needs once loaded)
@@ -943,7 +972,11 @@ int run_rsi(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int6
   T *so = (k < l) ? reinterpret_cast<T *>(ws + P->off_so) : S;
   T *vo = (k < l) ? reinterpret_cast<T *>(ws + P->off_vo) : V;
   const int64_t lduo = (k < l) ? l : ldu, ldvo = (k < l) ? l : ldv;
-  {
+  if constexpr (sizeof(T) == 4) {
+    // the small SVD of the Flip-Flop SRQR pipeline (column-block cluster Jacobi)
+    CK(launch_jacobi_blk(st, (const float *)w.mt, l, l, (float *)w.us, (float *)so, (float *)w.vs, w.ctl));
+    ++g_launches;
+  } else {
     // the small SVD of the Flip-Flop SRQR pipeline: QR of M^T, Jacobi on R^T,
     // Q of the small QR formed on the side stream
     const size_t qsmem = precond_qr_smem(l, sizeof(T));
@@ -1120,10 +1153,18 @@ int plan_jacobi(ffsrqr_plan_s *P) {
                           (const void *)jacobi_cluster_kernel<T, 2>, (const void *)jacobi_cluster_kernel<T, 4>,
                           (const void *)jacobi_cluster_kernel<T, 8>};
     for (const void *fn : fns) {
-      cudaFuncAttributes fa;
-      CK(cudaFuncGetAttributes(&fa, fn));
-      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              P->smem_optin - (int)fa.sharedSizeBytes));
+      CK(smem_cap_max(fn));
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    // single precision runs the column-block cluster Jacobi
+    if (jb_smem_bytes(k) + 1024 > (size_t)P->smem_optin) return FFSRQR_STATUS_UNSUPPORTED;
+    CK(smem_cap_max((const void *)jacobi_blk_kernel));
+    int nc = 0;
+    if (launch_jacobi_blk(nullptr, nullptr, k, k, nullptr, nullptr, nullptr, nullptr, true, &nc) != cudaSuccess ||
+        nc < 1) {
+      (void)cudaGetLastError();
+      return FFSRQR_STATUS_UNSUPPORTED;
     }
   }
   P->jac_cluster = 0;
@@ -1171,13 +1212,13 @@ int plan_qrcp(ffsrqr_plan_s *P) {
     grid = std::min<int64_t>(P->num_sms, grid * 2);
   }
   int per_sm = 0;
-  CK(cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->qrcp_smem));
+  CK(smem_cap_max((const void *)qrcp_kernel<T>));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel<T>, P->qrcp_threads, P->qrcp_smem));
   if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
   P->qrcp_grid = (int)grid;
   // swap loop: one co-resident block of 512 threads per SM
   P->swap_smem = (size_t)(P->k + 1 + 2 * P->k + 16 * P->k) * sizeof(T);
-  CK(cudaFuncSetAttribute(srqr_swap_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->swap_smem));
+  CK(smem_cap_max((const void *)srqr_swap_kernel<T>));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srqr_swap_kernel<T>, 512, P->swap_smem));
   if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
   P->swap_grid = P->num_sms;

@@ -72,7 +72,12 @@ def test_paper_size_1000_mixed():
     assert info["status"] == 0
     assert info["rank"] == int(sv_p)
     assert abs(info["nnz_e"] - nnz_p) <= 0.002 * nnz_p
-    assert abs(info["iters"] - it_p) <= 4
+    # the printed count is for tol 1e-7; the FP32 mode stops at tol 1e-6 (or
+    # when the residual stalls at its FP32 floor), one decade earlier: with
+    # the penalty growing by rho = 1.5 per iteration that is about
+    # log(10) / log(1.5) = 5.7 iterations fewer, so at most the printed count
+    # and at least 7 below it
+    assert it_p - 7 <= info["iters"] <= it_p
     assert np.linalg.norm(X - Xs) <= 1e-5 * np.linalg.norm(Xs)
 
 
