@@ -59,7 +59,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["mixed", "plain"], default="mixed")
+    ap.add_argument("--mode", choices=["mixed", "bf16x3", "plain"], default="mixed",
+                    help="mixed: TF32 sketch and three-product TF32 passes; bf16x3: BF16 sketch and "
+                         "three-product split-BF16 passes; plain: FP32 on the CUDA cores")
     ap.add_argument("--decay", choices=["slow", "fast"], default="slow")
     ap.add_argument("--m", type=int, default=20000)
     ap.add_argument("--n", type=int, default=20000)
@@ -214,10 +216,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the tensor-core kernel (else None)."""
-    path = os.path.join(ROOT, "profiles", "tc_pass_traffic.json")
+def ncu_traffic(kernel_key, mode):
+    """DRAM bytes per launch from the committed ncu summary of this mode's
+    tensor-core passes, if it was taken on the current source of the kernel
+    (else None)."""
+    if mode not in ("mixed", "bf16x3"):
+        return None
+    path = os.path.join(ROOT, "profiles", "tc_pass_traffic.json" if mode == "mixed" else
+                        "tc_pass_bf16_traffic.json")
     src = os.path.join(ROOT, "paper_1803_01982_gb300", "csrc", "tc_gemm.cuh")
     try:
         with open(path) as f:
@@ -299,7 +305,7 @@ def run_ours(a, rank, world, local_rank):
     from paper_1803_01982_gb300 import ffsrqr, synth
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     r = min(2000, a.m, a.n)
     A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=replica_seed(rank), device=str(dev))
     plan = ffsrqr.Plan(a.m, a.n, a.k, a.p, mode, flags=ffsrqr.FLAG_PHASE_TIMES, device=dev)
@@ -338,7 +344,7 @@ def run_ours(a, rank, world, local_rank):
 
     # roofline: the dominant pass kernel (one read of A per launch)
     bytes_per_launch = float(a.m) * a.n * 4
-    if mode == ffsrqr.MIXED:
+    if mode in (ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3):
         keys = ["tc_pass1_kernel", "tc_pass2_kernel", "tc_pass3_kernel"]
     else:
         keys = ["pass1_sketch", "pass2_r12", "pass3_tmp"]
@@ -348,7 +354,7 @@ def run_ours(a, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src,
             # the committed counters are scaled to the 20000 x 20000 workload
-            "traffic": ncu_traffic(dom) if (mode == ffsrqr.MIXED and a.m == 20000 and a.n == 20000) else None,
+            "traffic": ncu_traffic(dom, a.mode) if (a.m == 20000 and a.n == 20000) else None,
             "algorithmic_bytes_per_launch": bytes_per_launch}
     three_pass_ms = 3 * bytes_per_launch / (peak * 1e9) * 1e3
 
@@ -442,7 +448,7 @@ def run_batch(a):
         r = min(m, n, 256)
         mats.append(synth.decayed_torch(m, n, 0.9 ** np.arange(r), 1e-6, seed=1000 + i))
         sizes.append((m, n, k, 10))
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     b = ffsrqr.Batch(sizes, mode, streams=4)
     outs = b.outputs()
     chosen, tune_ms = b.tune(mats, outs)
@@ -470,7 +476,7 @@ def run_hosvd(a):
     unf = [T.reshape(400, 160000).contiguous(), T.permute(1, 0, 2).reshape(400, 160000).contiguous(),
            T.permute(2, 0, 1).reshape(400, 160000).contiguous()]
     del T
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     b = ffsrqr.Batch([(400, 160000, 40, 5)] * 3, mode, streams=3)
     outs = b.outputs()
     ms = _time_batch(a, b, unf, outs)
@@ -492,7 +498,7 @@ def run_tucker(a):
     from paper_1803_01982_gb300 import ffsrqr, synth
     dims, ranks = (400, 400, 400), (40, 40, 40)
     X = synth.tucker_torch(dims, ranks, 1e-4, seed=5)
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     st_method = a.workload == "sthosvd"
     t = ffsrqr.Tucker(dims, ranks, None, 5, mode, ffsrqr.TUCKER_STHOSVD if st_method else ffsrqr.TUCKER_HOSVD)
     out = t.outputs()
@@ -535,7 +541,7 @@ def run_rpca(a):
     m = a.m if a.m <= 4000 else 2000
     M, Xs, _ = synth.rpca_problem(m, m, m // 10, int(0.05 * m * m), seed=1)
     Md = torch.as_tensor(M).cuda()
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     s = ffsrqr.RPCA(m, m, mode)
     X = torch.empty_like(Md)
     E = torch.empty_like(Md)
@@ -584,7 +590,7 @@ def run_rsisvd(a):
     import torch
 
     from paper_1803_01982_gb300 import ffsrqr, synth
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     r = min(2000, a.m, a.n)
     A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=1)
     st = torch.cuda.current_stream()
@@ -644,7 +650,7 @@ def run_serving(a):
         XR = torch.randn(n, r, device="cuda", generator=gen)
         A = XL @ XR.T + 1e-3 * torch.randn(m, n, device="cuda", generator=gen)
         pool.append((A, r + 10))
-    mode = ffsrqr.MIXED if a.mode == "mixed" else ffsrqr.PLAIN_FP32
+    mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     srv = ffsrqr.Server(120 * (1 << 30), slots=8)
     # warm the plan cache and the kernels
     for A, k in pool[:4]:

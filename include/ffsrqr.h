@@ -36,16 +36,27 @@ extern "C" {
 typedef struct ffsrqr_plan_s *ffsrqr_plan_t;
 
 /* Arithmetic modes (the precision layer).
- *   FFSRQR_PLAIN_FP32: every product in FP32 on the CUDA cores (FFMA).
- *   FFSRQR_MIXED:      the sketch B = Omega A on the tensor cores in TF32
- *                      (one product; the sketch only chooses pivots), the two
- *                      accuracy-bearing passes (Q1^T A and A Pi Qhat1) on the
- *                      tensor cores as a three-product TF32 split that
- *                      recovers FP32 accuracy; everything else FP32.
- *   FFSRQR_FP64:       everything in FP64 on the CUDA cores (A, U, S, V are
- *                      double). */
+ *   FFSRQR_PLAIN_FP32:   every product in FP32 on the CUDA cores (FFMA).
+ *   FFSRQR_MIXED_TF32X3: the sketch B = Omega A on the tensor cores in TF32
+ *                        (one product; the sketch only chooses pivots), the
+ *                        two accuracy-bearing passes (Q1^T A and A Pi Qhat1)
+ *                        on the tensor cores as a three-product TF32 split
+ *                        that recovers FP32 accuracy; everything else FP32.
+ *                        FFSRQR_MIXED is the same value.
+ *   FFSRQR_MIXED_BF16X3: the sketch in BF16 (one product), the two passes as
+ *                        a three-product split-BF16 (head x head + head x
+ *                        tail + tail x head, FP32 accumulate: about 2^-16
+ *                        per product, random, so sigma stays within the FP32
+ *                        tolerances); BF16 runs the tensor cores at twice the
+ *                        TF32 rate, so the passes are bound by HBM, not by
+ *                        the three products.  The Grams and small products
+ *                        stay three-product TF32.
+ *   FFSRQR_FP64:         everything in FP64 on the CUDA cores (A, U, S, V are
+ *                        double). */
 #define FFSRQR_PLAIN_FP32 0
+#define FFSRQR_MIXED_TF32X3 1
 #define FFSRQR_MIXED 1
+#define FFSRQR_MIXED_BF16X3 2
 #define FFSRQR_FP64 3
 
 /* Numerical status codes (ffsrqr_info_t.status and positive return codes). */

@@ -77,6 +77,9 @@ struct Item {
 
 }  // namespace
 
+// The two mixed modes run the passes on the tensor cores.
+inline bool tc_mode(int mode) { return mode == FFSRQR_MIXED_TF32X3 || mode == FFSRQR_MIXED_BF16X3; }
+
 // Shared with the batch and server translation units (not part of the C ABI).
 void ffq_set_last_error(const char *what, cudaError_t e) { cuda_ok(e, what); }
 
@@ -97,7 +100,8 @@ struct ffsrqr_plan_s {
   size_t off_q1, off_w, off_rc1, off_rc2, off_gt, off_r11, off_rinv, off_zt, off_bjt, off_cbt,
       off_r, off_bv, off_bi, off_avec, off_z, off_hpart, off_npart, off_vp, off_rz, off_tmp,
       off_yt, off_rt, off_t1, off_mt, off_us, off_vs, off_qv, off_qg, off_part, off_sgnv, off_sgni, off_sgn;
-  size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (FFSRQR_MIXED)
+  size_t off_tcpart, off_tt, off_bh, off_bl;  // tensor-core passes (the mixed modes)
+  size_t off_omb;                             // BF16 copy of Omega (FFSRQR_MIXED_BF16X3)
   size_t off_sinv, off_sh, off_sl, off_scr;   // tensor-core small products (FFSRQR_MIXED)
   int jac_cluster, jac_lpp;                   // blocks of the Jacobi cluster, lanes per pair
   cudaStream_t side = nullptr;                // forms Q of the small QR while the Jacobi runs
@@ -201,22 +205,25 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D FP32 tensor map over a row-major (outer x inner) array with leading
-// dimension ld (elements), box (box_inner x box_outer), 64B/128B swizzle.
-bool make_map(CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, int64_t ld,
-              int box_inner, int box_outer) {
+// 2-D tensor map over a row-major (outer x inner) array of FP32 (or BF16,
+// bf = true) with leading dimension ld (elements), box (box_inner x
+// box_outer), 64B/128B swizzle by the box row's bytes.
+bool make_map(CUtensorMap *map, const void *ptr, int64_t inner, int64_t outer, int64_t ld,
+              int box_inner, int box_outer, bool bf = false) {
   auto fn = encode_fn();
   if (!fn) {
     g_last_cuda_error = "cuTensorMapEncodeTiled entry point unavailable";
     return false;
   }
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const int el = bf ? 2 : 4;
+  cuuint64_t strides[1] = {(cuuint64_t)ld * el};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapSwizzle swz =
-      (box_inner * 4 == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box,
+      (box_inner * el == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  CUresult r = fn(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void *>(ptr), dims, strides, box,
                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -234,10 +241,11 @@ bool make_map(CUtensorMap *map, const float *ptr, int64_t inner, int64_t outer, 
 // rows (passes 1, 2) or its columns (pass 3).  Bt / Btl: thin operand (and its
 // TF32 tail for nprod = 3) stored N x K row-major with leading dim ldb.
 // pass 0..2 records the pass-kernel events; -1 for the other products.
+// bf: BF16 operands (Bt / Btl are BF16 arrays, A is converted on chip).
 int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pass, int nprod, bool a_mn, int M,
-              int N, int K, const float *A, int64_t lda, const float *Bt, const float *Btl, int64_t ldb,
-              float *C, int64_t ldc) {
-  const int BK = (nprod == 1) ? 32 : 16;
+              int N, int K, const float *A, int64_t lda, const void *Bt, const void *Btl, int64_t ldb,
+              float *C, int64_t ldc, bool bf = false) {
+  const int BK = (nprod == 1 || bf) ? 32 : 16;
   const int ntile = (int)round_up(N, 16);
   if (ntile > TC_MAX_NT) return FFSRQR_STATUS_UNSUPPORTED;
   CUtensorMap mA, mB, mBl;
@@ -247,8 +255,8 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   } else {
     if (!make_map(&mA, A, K, M, lda, BK, TC_BM)) return FFSRQR_STATUS_CUDA;
   }
-  if (!make_map(&mB, Bt, K, N, ldb, BK, ntile)) return FFSRQR_STATUS_CUDA;
-  if (!make_map(&mBl, Btl ? Btl : Bt, K, N, ldb, BK, ntile)) return FFSRQR_STATUS_CUDA;
+  if (!make_map(&mB, Bt, K, N, ldb, BK, ntile, bf)) return FFSRQR_STATUS_CUDA;
+  if (!make_map(&mBl, Btl ? Btl : Bt, K, N, ldb, BK, ntile, bf)) return FFSRQR_STATUS_CUDA;
   TcSched sc;
   sc.M = M;
   sc.N = N;
@@ -271,24 +279,30 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   sc.whole_tiles = (sc.KB <= 64) ? 1 : 0;
   if (sc.whole_tiles) sc.G = std::min(sc.G, sc.tiles);
   int stage_bytes = 0;
-  if (nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true>::bytes(ntile);
+  if (bf && nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true, true>::bytes(ntile);
+  else if (bf && nprod == 3 && a_mn) stage_bytes = TcStage<32, 3, true, true>::bytes(ntile);
+  else if (bf && nprod == 3) stage_bytes = TcStage<32, 3, false, true>::bytes(ntile);
+  else if (nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true>::bytes(ntile);
   else if (nprod == 3 && a_mn) stage_bytes = TcStage<16, 3, true>::bytes(ntile);
   else stage_bytes = TcStage<16, 3, false>::bytes(ntile);
   const int budget = P->smem_optin - 2048;  // static shared memory and alignment slack
   sc.stages = std::min(TC_MAX_STAGES, budget / stage_bytes);
   if (sc.stages < 2) return FFSRQR_STATUS_UNSUPPORTED;
   const size_t smem = (size_t)sc.stages * stage_bytes + 1024;
-#define TC_LAUNCH(BKv, NPv, AMNv)                                                                    \
+#define TC_LAUNCH(BKv, NPv, AMNv, BFv)                                                               \
   {                                                                                                  \
-    auto fn = tc_gemm_kernel<BKv, NPv, AMNv>;                                                        \
+    auto fn = tc_gemm_kernel<BKv, NPv, AMNv, BFv>;                                                   \
     CK(smem_cap_max((const void *)fn));                                                               \
     if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[P->evset][pass][0], st);                     \
     fn<<<sc.G, TC_THREADS, smem, st>>>(mA, mB, mBl, sc);                                             \
     if (P->ev_ok && pass >= 0) cudaEventRecord(P->ev_tc[P->evset][pass][1], st);                     \
   }
-  if (nprod == 1 && a_mn) TC_LAUNCH(32, 1, true)
-  else if (nprod == 3 && a_mn) TC_LAUNCH(16, 3, true)
-  else if (nprod == 3 && !a_mn) TC_LAUNCH(16, 3, false)
+  if (bf && nprod == 1 && a_mn) TC_LAUNCH(32, 1, true, true)
+  else if (bf && nprod == 3 && a_mn) TC_LAUNCH(32, 3, true, true)
+  else if (bf && nprod == 3 && !a_mn) TC_LAUNCH(32, 3, false, true)
+  else if (!bf && nprod == 1 && a_mn) TC_LAUNCH(32, 1, true, false)
+  else if (!bf && nprod == 3 && a_mn) TC_LAUNCH(16, 3, true, false)
+  else if (!bf && nprod == 3 && !a_mn) TC_LAUNCH(16, 3, false, false)
   else return FFSRQR_STATUS_UNSUPPORTED;
 #undef TC_LAUNCH
   CKL("tc_gemm");
@@ -470,7 +484,7 @@ template <typename T>
 bool use_tc(const ffsrqr_plan_s *P, const T *A, int64_t lda) {
   // the tensor-core epilogue holds N tiles of up to TC_MAX_NT columns (the
   // sketch has s columns); wider problems run the CUDA-core passes
-  return sizeof(T) == 4 && P->mode == FFSRQR_MIXED && tc_ok(A, lda) && round_up(P->s, 16) <= TC_MAX_NT;
+  return sizeof(T) == 4 && tc_mode(P->mode) && tc_ok(A, lda) && round_up(P->s, 16) <= TC_MAX_NT;
 }
 
 // Pass 2 (a_mn: G^T = A^T X, X = Q1 with rows = m) or pass 3 (tmp = A X,
@@ -479,6 +493,17 @@ bool use_tc(const ffsrqr_plan_s *P, const T *A, int64_t lda) {
 int tc_thin_pass(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, bool a_mn, const float *A,
                  int64_t lda, const float *X, int64_t rows, float *C) {
   const int k = P->k;
+  const int M = (int)(a_mn ? P->n : P->m);
+  if (P->mode == FFSRQR_MIXED_BF16X3) {
+    // BF16 head and tail of X^T (k x rows, K-major), one transposing pass
+    const int64_t ldb = round_up(rows, 8);
+    __nv_bfloat16 *bh = reinterpret_cast<__nv_bfloat16 *>(ws + P->off_bh);
+    __nv_bfloat16 *bl = reinterpret_cast<__nv_bfloat16 *>(ws + P->off_bl);
+    transpose_split_bf16_kernel<<<dim3((unsigned)cdiv(rows, 32), (unsigned)cdiv(k, 32)), dim3(32, 8), 0, st>>>(
+        X, P->ldk, rows, k, bh, bl, ldb);
+    CKL("transpose_split_bf16");
+    return launch_tc(st, P, ws, a_mn ? 1 : 2, 3, a_mn, M, k, (int)rows, A, lda, bh, bl, ldb, C, P->ldk, true);
+  }
   const int64_t ldt = round_up(rows, 4);
   float *tt = reinterpret_cast<float *>(ws + P->off_tt);
   float *bh = reinterpret_cast<float *>(ws + P->off_bh);
@@ -489,7 +514,6 @@ int tc_thin_pass(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, boo
   split_tf32_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)k * rows, 256), 8 * P->num_sms), 256, 0, st>>>(
       tt, ldt, k, rows, bh, bl);
   CKL("split_tf32");
-  const int M = (int)(a_mn ? P->n : P->m);
   return launch_tc(st, P, ws, a_mn ? 1 : 2, 3, a_mn, M, k, (int)rows, A, lda, bh, bl, ldt, C, P->ldk);
 }
 
@@ -683,7 +707,17 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   const bool tc = use_tc<T>(P, A, lda);
   MARK(1);
   // a2: pass 1, B^T (n x s) = A^T Omega^T
-  if (tc) {
+  if (tc && P->mode == FFSRQR_MIXED_BF16X3) {
+    // BF16 sketch: Omega rounded to BF16 once, A converted on chip
+    const int64_t ldb = round_up(m, 8);
+    __nv_bfloat16 *omb = reinterpret_cast<__nv_bfloat16 *>(ws + P->off_omb);
+    to_bf16_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)s * m, 256), 8 * nsm), 256, 0, st>>>(
+        (const float *)w.om, ldm, s, m, omb, ldb);
+    CKL("to_bf16");
+    if ((rc = launch_tc(st, P, ws, 0, 1, true, (int)n, s, (int)m, (const float *)A, lda, omb, nullptr, ldb,
+                        (float *)w.bt, lds, true)))
+      return rc;
+  } else if (tc) {
     if ((rc = launch_tc(st, P, ws, 0, 1, true, (int)n, s, (int)m, (const float *)A, lda, (const float *)w.om,
                         nullptr, ldm, (float *)w.bt, lds)))
       return rc;
@@ -1095,8 +1129,10 @@ void layout(ffsrqr_plan_s *P) {
   P->off_sgn = take((size_t)k * E);
   P->part_cap = (size_t)std::max<int64_t>((int64_t)k * k * 64, (int64_t)4 * 1024 * 1024 / E);
   P->off_part = take(P->part_cap * E);
-  if (P->mode == FFSRQR_MIXED) {
-    const int64_t ldmax = std::max(round_up(m, 4), round_up(n, 4));
+  P->off_omb = 0;
+  if (tc_mode(P->mode)) {
+    const int64_t ldmax = std::max(round_up(m, 8), round_up(n, 8));
+    if (P->mode == FFSRQR_MIXED_BF16X3) P->off_omb = take((size_t)s * round_up(m, 8) * 2);  // BF16 Omega
     P->off_tcpart = take((size_t)2 * nsm * TC_BM * 256 * sizeof(float));
     P->off_tt = take((size_t)k * ldmax * sizeof(float));
     P->off_bh = take((size_t)k * ldmax * sizeof(float));
@@ -1249,7 +1285,8 @@ int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32
   const int sh = (kout == k) ? 0 : 1;  // ffsrqr_plan has no l argument
   if (k < 1 || k > n || k > m) return -4 - sh;
   if (p < 0 || (int64_t)k + p > m || k + p > 256) return -5 - sh;
-  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -6 - sh;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64)
+    return -6 - sh;
   if (opts && !(opts->g > 1.0)) return -7 - sh;
   if (opts && opts->max_swaps < 0) return -7 - sh;
   if (!workspace_bytes) return -8 - sh;
@@ -1437,7 +1474,8 @@ int ffsrqr_plan_rsi(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_
   if (k < 1 || k > n || k > m) return -4;
   if (p < 0 || (int64_t)k + p > std::min(m, n)) return -5;
   if (q < 0) return -6;
-  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -7;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64)
+    return -7;
   if (opts && (!(opts->g > 1.0) || opts->max_swaps < 0)) return -8;
   if (!workspace_bytes) return -9;
   // a plan at width l = k + p (no sketch oversampling of its own) whose
@@ -1516,7 +1554,7 @@ int ffsrqr_phase_times_back(ffsrqr_plan_t plan, int32_t back, float *ms, int32_t
   }
   for (int i = 0; i < 3 && cnt < cap; ++i, ++cnt) {
     float t = -1.f;
-    if (plan->mode == FFSRQR_MIXED &&
+    if (tc_mode(plan->mode) &&
         cudaEventElapsedTime(&t, plan->ev_tc[e][i][0], plan->ev_tc[e][i][1]) != cudaSuccess)
       t = -1.f;
     ms[cnt] = t;

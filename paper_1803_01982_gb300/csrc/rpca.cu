@@ -344,7 +344,7 @@ int ffsrqr_rpca_create(ffsrqr_rpca_t *out, int64_t m, int64_t n, const ffsrqr_rp
   ffsrqr_rpca_opts_t o{};
   if (opts) o = *opts;
   const int mode = opts ? o.mode : FFSRQR_MIXED;
-  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -4;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64) return -4;
   if (opts && (o.rho < 0 || o.tol < 0 || o.mu_bar_ratio < 0 || o.lambda < 0)) return -4;
   ffsrqr_rpca_s *R = new (std::nothrow) ffsrqr_rpca_s();
   if (!R) return FFSRQR_STATUS_WORKSPACE;

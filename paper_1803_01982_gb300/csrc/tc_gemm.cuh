@@ -34,11 +34,18 @@
 // buffers (256 columns each) let the MMA fill one chunk while the epilogue
 // drains the other.
 //
-// Warp roles (12 warps, so that at most three share an SM sub-partition's
-// register file at 168 registers each): 0 = TMA producer, 1 = TMEM
-// allocation owner and MMA issuer (one thread), 2..9 = epilogue (warp w reads
-// TMEM lanes 32*(w%4)..+31; warps 2..5 take the first half of the columns,
-// 6..9 the second), 10..11 = converters.
+// Warp roles (16 warps, by warpgroup; see TC_THREADS below): the TMA
+// producer and the MMA issuer (one thread each) share the first warpgroup
+// with two converter warps, two warpgroups drain TMEM (epilogue), and a
+// fourth warpgroup converts.  Registers move from the converter groups to the
+// epilogue groups with setmaxnreg, so six converter warps fit beside
+// epilogue warps that hold up to 112 accumulators each.
+//
+// BF16 operands (kind::f16, the split-BF16 mode): A lands as FP32 and the
+// converters write its BF16 head and tail (round to nearest even) as K-major
+// rows of 32 BF16 values; the thin operand comes split to BF16 from global
+// memory; D = Ah Bh + Ah Bl + Al Bh with FP32 accumulation (about 2^-16 per
+// product).  The one-product BF16 sketch keeps the head only.
 //
 // Stream-K: unit u = tile*KB + kb; block c owns units [U*c/G, U*(c+1)/G).  A
 // block's first and last segments may cover part of a tile's K range; those
@@ -51,6 +58,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -58,8 +66,21 @@
 namespace ffq {
 
 constexpr int TC_BM = 128;
-constexpr int TC_CONV_WARPS = 2;
-constexpr int TC_THREADS = 32 * (2 + 8 + TC_CONV_WARPS);  // 12 warps: <= 3 per SM sub-partition
+// Warp roles, by warpgroup (four warps each):
+//   WG0: warp 0 TMA producer, warp 1 TMEM owner and MMA issuer, warps 2-3 converters;
+//   WG1, WG2: epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31; WG1 takes
+//             the first half of the columns, WG2 the second);
+//   WG3: converters.
+// The block is launched with 128 registers per thread (65536 / 512); WG0 and
+// WG3 give theirs down to TC_REG_LOW, WG1 and WG2 take TC_REG_HIGH (the
+// epilogue holds up to 112 FP32 accumulators per thread):
+// 128 (2 TC_REG_LOW + 2 TC_REG_HIGH) = 128 * 512 = 65536, the launch's total.
+constexpr int TC_CONV_WARPS = 6;
+constexpr int TC_THREADS = 512;
+constexpr int TC_REG_LOW = 88;
+constexpr int TC_REG_HIGH = 168;
+static_assert(128 * (2 * TC_REG_LOW + 2 * TC_REG_HIGH) == 65536, "register split must equal the launch's total");
+static_assert(TC_THREADS * 128 == 65536, "launched at 128 registers per thread");
 constexpr int TC_CHUNK = 8;      // K-blocks per TMEM accumulation chunk (3-product kernels)
 constexpr int TC_MAX_NT = 224;   // widest N tile (columns) the epilogue registers hold
 constexpr int TC_EPI_WARPS = 8;
@@ -162,6 +183,20 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f16 with BF16 A and B, FP32 accumulate,
+// M = 128, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
   asm volatile(
@@ -244,32 +279,65 @@ __device__ __forceinline__ uint32_t mn_off(int k, int m) {
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// Byte offset of the 16-byte chunk holding BF16 elements (r, 8 c .. 8 c + 7)
+// of a K-major tile whose rows are 32 BF16 values (64 bytes, 64B swizzle:
+// the chunk index XORed with address bits 7..8, as the MMA reads it).
+__device__ __forceinline__ uint32_t kmajor_bf16_chunk(int r, int c) {
+  return (uint32_t)(r * 64 + (((c ^ (r >> 1)) & 3) << 4));
+}
+
+// Eight FP32 values -> their BF16 heads (round to nearest even) and, with
+// TAIL, the BF16 of what the heads leave (x - head, exact in FP32), each
+// packed as one 16-byte chunk.
+template <bool TAIL>
+__device__ __forceinline__ void bf16_split8(const float *x, uint4 &h, uint4 &l) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+    hw[i] = *reinterpret_cast<const uint32_t *>(&hb);
+    if (TAIL) {
+      const float2 hf = __bfloat1622float2(hb);
+      const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+      lw[i] = *reinterpret_cast<const uint32_t *>(&lb);
+    }
+  }
+  h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  if (TAIL) l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
 // Shared memory of one stage: [raw A landing (A_MN only)] [Ah] [Al (NPROD 3)]
 // [Bh] [Bl (NPROD 3)]; every piece is a multiple of 1024 bytes.
-template <int BK, int NPROD, bool A_MN>
+// BF: the operands are BF16 (kind::f16): A lands as FP32 (BK columns, 128 B
+// rows) and the converters write its BF16 head (and tail) as K-major rows of
+// BK = 32 BF16 values (64 bytes); the thin operand comes as BF16 from global
+// memory.
+template <int BK, int NPROD, bool A_MN, bool BF = false>
 struct TcStage {
-  static constexpr int A_BYTES = TC_BM * BK * 4;
-  static constexpr int RAW = A_MN ? A_BYTES : 0;
+  static constexpr int EL = BF ? 2 : 4;                    // operand element bytes
+  static constexpr int A_BYTES = TC_BM * BK * EL;          // one operand tile of A
+  static constexpr int RAW_BYTES = TC_BM * BK * 4;         // the FP32 landing tile
+  static constexpr int RAW = (A_MN || BF) ? RAW_BYTES : 0;
   static constexpr int AH = RAW;
   static constexpr int AL = AH + A_BYTES;
   static constexpr int BH = AH + A_BYTES * (NPROD == 3 ? 2 : 1);
-  __host__ __device__ static constexpr int b_bytes(int nt) { return nt * BK * 4; }
+  __host__ __device__ static constexpr int b_bytes(int nt) { return nt * BK * EL; }
   __host__ __device__ static constexpr int bytes(int nt) { return BH + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
-  __host__ __device__ static constexpr int tx(int nt) { return A_BYTES + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
-  static constexpr bool CONVERT = A_MN || NPROD == 3;
+  __host__ __device__ static constexpr int tx(int nt) { return RAW_BYTES + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
+  static constexpr bool CONVERT = A_MN || NPROD == 3 || BF;
 };
 
-template <int BK, int NPROD, bool A_MN>
-__global__ void __maxnreg__(168)
+template <int BK, int NPROD, bool A_MN, bool BF = false>
+__global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmBl, TcSched sc) {
-  using S = TcStage<BK, NPROD, A_MN>;
+  using S = TcStage<BK, NPROD, A_MN, BF>;
   // the single-product sketch keeps whole segments in TMEM: its accuracy is
   // set by the TF32 operands, not by the accumulation
   constexpr int CHUNK = (NPROD == 3) ? TC_CHUNK : (1 << 30);
   constexpr int A_BYTES = S::A_BYTES;
-  constexpr int KSWZ = (BK == 32) ? 2 : 4;  // 128B / 64B swizzle of K-major rows
-  constexpr int KROW = BK * 4;
+  constexpr int KROW = BK * S::EL;             // bytes of a K-major operand row
+  constexpr int KSWZ = (KROW == 128) ? 2 : 4;  // 128B / 64B swizzle of K-major rows
   const int NT = sc.ntile;
   const int STAGES = sc.stages;
   const int B_BYTES = S::b_bytes(NT);
@@ -323,117 +391,237 @@ __global__ void __maxnreg__(168)
   const uint32_t tmem = tmem_base;
   volatile int *abortp = &abort_flag;
 
+
   auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE_BYTES; };
 
-  if (warp == 0) {
-    // ---------------- TMA producer ----------------
-    if (lane == 0) {
-      int s = 0;
-      uint32_t ph = 0;
-      int tile, kb0, kb1;
-      SegIter my = it;
-      bool ok = true;
-      uint32_t issued = 0, issued_ph = 0;  // per stage: a load in flight, and its phase parity
-      while (ok && my.next(tile, kb0, kb1)) {
-        for (int kb = kb0; kb < kb1 && ok; ++kb) {
-          if (!mbar_wait(&empty_bar[s], ph ^ 1u, abortp, sc.ctl)) {
-            ok = false;
-            break;
-          }
-          issued |= 1u << s;
-          issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
-          unsigned char *st = stage_ptr(s);
-          mbar_expect_tx(&full_bar[s], TX_BYTES);
-          const int k0 = kb * BK, m0 = tile * TC_BM;
-          if (A_MN) {
+  // Roles by warpgroup; each warpgroup's branch starts with its register
+  // share (setmaxnreg is warpgroup-wide, so all four warps of a group execute
+  // the same instruction).
+  auto converters = [&]() {
+    // ---------------- converters (warps 2-3 and 12-15) ----------------
+    constexpr int NCT = 32 * TC_CONV_WARPS;
+    const int ct = ((warp < 4) ? warp - 2 : warp - 10) * 32 + lane;  // 0..NCT-1
+    int s = 0;
+    uint32_t ph = 0;
+    int tile, kb0, kb1;
+    SegIter my = it;
+    bool ok = true;
+    while (ok && my.next(tile, kb0, kb1)) {
+      for (int kb = kb0; kb < kb1; ++kb) {
+        if (!mbar_wait(&full_bar[s], ph, abortp, sc.ctl)) {
+          ok = false;
+          break;
+        }
+        unsigned char *st = stage_ptr(s);
+        if constexpr (BF) {
+          // FP32 landing -> K-major BF16 head (and tail): task = (row m, 8
+          // consecutive k), 128 rows x BK / 8 chunks per stage; consecutive
+          // threads take consecutive m (conflict-free landing reads)
+#pragma unroll 1
+          for (int task = ct; task < TC_BM * (BK / 8); task += NCT) {
+            const int m = task % TC_BM, c8 = task / TC_BM;
+            float x[8];
+            if (A_MN) {
 #pragma unroll
-            for (int q = 0; q < TC_BM / 32; ++q)
-              tma_load_2d(st + q * (BK * 128), &tmA, m0 + 32 * q, k0, &full_bar[s]);
-          } else {
-            tma_load_2d(st + S::AH, &tmA, k0, m0, &full_bar[s]);
+              for (int j = 0; j < 8; ++j) x[j] = *reinterpret_cast<const float *>(st + mn_off<BK>(8 * c8 + j, m));
+            } else {
+              const float4 v0 = *reinterpret_cast<const float4 *>(st + kmajor_off<32>(m, 8 * c8));
+              const float4 v1 = *reinterpret_cast<const float4 *>(st + kmajor_off<32>(m, 8 * c8 + 4));
+              x[0] = v0.x;
+              x[1] = v0.y;
+              x[2] = v0.z;
+              x[3] = v0.w;
+              x[4] = v1.x;
+              x[5] = v1.y;
+              x[6] = v1.z;
+              x[7] = v1.w;
+            }
+            uint4 h, l;
+            bf16_split8<NPROD == 3>(x, h, l);
+            const uint32_t o = kmajor_bf16_chunk(m, c8);
+            *reinterpret_cast<uint4 *>(st + S::AH + o) = h;
+            if (NPROD == 3) *reinterpret_cast<uint4 *>(st + S::AL + o) = l;
           }
-          tma_load_2d(st + S::BH, &tmB, k0, 0, &full_bar[s]);
-          if (NPROD == 3) tma_load_2d(st + S::BH + B_BYTES, &tmBl, k0, 0, &full_bar[s]);
-          if (++s == STAGES) {
-            s = 0;
-            ph ^= 1u;
+        } else if (A_MN) {
+          // transpose rows m = ct, ct + NCT, ... of the m-contiguous tile
+          // into K-major rows
+#pragma unroll 1
+          for (int m = ct; m < TC_BM; m += NCT)
+#pragma unroll 4
+          for (int k4 = 0; k4 < BK; k4 += 4) {
+            float x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = *reinterpret_cast<const float *>(st + mn_off<BK>(k4 + j, m));
+            const uint32_t o = kmajor_off<BK>(m, k4);
+            if (NPROD == 3) {
+              float4 h, l;
+              h.x = tf32_head(x[0]);
+              h.y = tf32_head(x[1]);
+              h.z = tf32_head(x[2]);
+              h.w = tf32_head(x[3]);
+              l.x = x[0] - h.x;
+              l.y = x[1] - h.y;
+              l.z = x[2] - h.z;
+              l.w = x[3] - h.w;
+              *reinterpret_cast<float4 *>(st + S::AH + o) = h;
+              *reinterpret_cast<float4 *>(st + S::AL + o) = l;
+            } else {
+              *reinterpret_cast<float4 *>(st + S::AH + o) = make_float4(x[0], x[1], x[2], x[3]);
+            }
+          }
+        } else {
+          // split the K-major tile in place: Ah (TF32 head) and Al (tail)
+          float4 *a4 = reinterpret_cast<float4 *>(st + S::AH);
+          float4 *l4 = reinterpret_cast<float4 *>(st + S::AL);
+#pragma unroll 4
+          for (int i = ct; i < A_BYTES / 16; i += NCT) {
+            const float4 x = a4[i];
+            float4 h, l;
+            h.x = tf32_head(x.x);
+            h.y = tf32_head(x.y);
+            h.z = tf32_head(x.z);
+            h.w = tf32_head(x.w);
+            l.x = x.x - h.x;
+            l.y = x.y - h.y;
+            l.z = x.z - h.z;
+            l.w = x.w - h.w;
+            a4[i] = h;
+            l4[i] = l;
           }
         }
-      }
-      if (!ok) {
-        for (int d = 0; d < STAGES; ++d)
-          if (issued & (1u << d)) mbar_wait_quiet(&full_bar[d], (issued_ph >> d) & 1u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv_bar[s]);
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
     }
-    __syncwarp();
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      int s = 0;
-      uint32_t ph = 0;
-      int chunk = 0;
-      int tile, kb0, kb1;
-      SegIter my = it;
-      const uint32_t IDESC = idesc_tf32(NT);
-      bool ok = true;
-      while (ok && my.next(tile, kb0, kb1)) {
-        for (int kc = kb0; kc < kb1 && ok; kc += CHUNK) {
-          const int kc1 = (kb1 - kc > CHUNK) ? kc + CHUNK : kb1;
-          const int b = chunk & 1;
-          const uint32_t acc_ph = (uint32_t)((chunk >> 1) & 1);
-          if (!mbar_wait(&acce_bar[b], acc_ph ^ 1u, abortp, sc.ctl)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t dt = tmem + (uint32_t)(b * 256);
-          for (int kb = kc; kb < kc1; ++kb) {
-            uint64_t *wb = S::CONVERT ? &conv_bar[s] : &full_bar[s];
-            if (!mbar_wait(wb, ph, abortp, sc.ctl)) {
+    };
+  const int wg = warp >> 2;
+  if (wg == 0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TC_REG_LOW));
+    if (warp == 0) {
+      // ---------------- TMA producer ----------------
+      if (lane == 0) {
+        int s = 0;
+        uint32_t ph = 0;
+        int tile, kb0, kb1;
+        SegIter my = it;
+        bool ok = true;
+        uint32_t issued = 0, issued_ph = 0;  // per stage: a load in flight, and its phase parity
+        while (ok && my.next(tile, kb0, kb1)) {
+          for (int kb = kb0; kb < kb1 && ok; ++kb) {
+            if (!mbar_wait(&empty_bar[s], ph ^ 1u, abortp, sc.ctl)) {
               ok = false;
               break;
             }
-            tc_fence_after();
-            const uint32_t base = smem_u32(stage_ptr(s));
-            const uint32_t ah = base + S::AH, al = base + S::AL, bh = base + S::BH, bl = bh + B_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 8; ++kk) {
-              // K-major operands: rows of BK*4 bytes in 8-row groups; K step of
-              // one MMA (8 TF32 values) = 32 bytes within the swizzled row.
-              const uint64_t da = smem_desc(ah + kk * 32, 16, 8 * KROW, KSWZ);
-              const uint64_t db = smem_desc(bh + kk * 32, 16, 8 * KROW, KSWZ);
-              const uint32_t acc = (kb > kc || kk > 0) ? 1u : 0u;
-              mma_tf32(dt, da, db, IDESC, acc);
-              if (NPROD == 3) {
-                const uint64_t dal = smem_desc(al + kk * 32, 16, 8 * KROW, KSWZ);
-                const uint64_t dbl = smem_desc(bl + kk * 32, 16, 8 * KROW, KSWZ);
-                mma_tf32(dt, da, dbl, IDESC, 1u);
-                mma_tf32(dt, dal, db, IDESC, 1u);
-              }
+            issued |= 1u << s;
+            issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+            unsigned char *st = stage_ptr(s);
+            mbar_expect_tx(&full_bar[s], TX_BYTES);
+            const int k0 = kb * BK, m0 = tile * TC_BM;
+            if (A_MN) {
+  #pragma unroll
+              for (int q = 0; q < TC_BM / 32; ++q)
+                tma_load_2d(st + q * (BK * 128), &tmA, m0 + 32 * q, k0, &full_bar[s]);
+            } else {
+              tma_load_2d(st + (BF ? 0 : S::AH), &tmA, k0, m0, &full_bar[s]);
             }
-            mma_commit(&empty_bar[s]);
+            tma_load_2d(st + S::BH, &tmB, k0, 0, &full_bar[s]);
+            if (NPROD == 3) tma_load_2d(st + S::BH + B_BYTES, &tmBl, k0, 0, &full_bar[s]);
             if (++s == STAGES) {
               s = 0;
               ph ^= 1u;
             }
           }
-          if (!ok) break;
-          mma_commit(&accf_bar[b]);
-          ++chunk;
+        }
+        if (!ok) {
+          for (int d = 0; d < STAGES; ++d)
+            if (issued & (1u << d)) mbar_wait_quiet(&full_bar[d], (issued_ph >> d) & 1u);
         }
       }
-      if (*abortp) {
-        // make sure no MMA is still writing TMEM before it is freed
-        mma_commit(&drain_bar);
-        mbar_wait_quiet(&drain_bar, 0);
+      __syncwarp();
+    } else if (warp == 1) {
+      // ---------------- MMA issuer ----------------
+      if (lane == 0) {
+        int s = 0;
+        uint32_t ph = 0;
+        int chunk = 0;
+        int tile, kb0, kb1;
+        SegIter my = it;
+        const uint32_t IDESC = BF ? idesc_bf16(NT) : idesc_tf32(NT);
+        bool ok = true;
+        while (ok && my.next(tile, kb0, kb1)) {
+          for (int kc = kb0; kc < kb1 && ok; kc += CHUNK) {
+            const int kc1 = (kb1 - kc > CHUNK) ? kc + CHUNK : kb1;
+            const int b = chunk & 1;
+            const uint32_t acc_ph = (uint32_t)((chunk >> 1) & 1);
+            if (!mbar_wait(&acce_bar[b], acc_ph ^ 1u, abortp, sc.ctl)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dt = tmem + (uint32_t)(b * 256);
+            for (int kb = kc; kb < kc1; ++kb) {
+              uint64_t *wb = S::CONVERT ? &conv_bar[s] : &full_bar[s];
+              if (!mbar_wait(wb, ph, abortp, sc.ctl)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t base = smem_u32(stage_ptr(s));
+              const uint32_t ah = base + S::AH, al = base + S::AL, bh = base + S::BH, bl = bh + B_BYTES;
+              // K-major operands: rows of KROW bytes in 8-row groups; the K step
+              // of one MMA (8 TF32 or 16 BF16 values) is 32 bytes within the
+              // swizzled row.
+  #pragma unroll
+              for (int kk = 0; kk < KROW / 32; ++kk) {
+                const uint64_t da = smem_desc(ah + kk * 32, 16, 8 * KROW, KSWZ);
+                const uint64_t db = smem_desc(bh + kk * 32, 16, 8 * KROW, KSWZ);
+                const uint32_t acc = (kb > kc || kk > 0) ? 1u : 0u;
+                if constexpr (BF) mma_bf16(dt, da, db, IDESC, acc);
+                else mma_tf32(dt, da, db, IDESC, acc);
+                if (NPROD == 3) {
+                  const uint64_t dal = smem_desc(al + kk * 32, 16, 8 * KROW, KSWZ);
+                  const uint64_t dbl = smem_desc(bl + kk * 32, 16, 8 * KROW, KSWZ);
+                  if constexpr (BF) {
+                    mma_bf16(dt, da, dbl, IDESC, 1u);
+                    mma_bf16(dt, dal, db, IDESC, 1u);
+                  } else {
+                    mma_tf32(dt, da, dbl, IDESC, 1u);
+                    mma_tf32(dt, dal, db, IDESC, 1u);
+                  }
+                }
+              }
+              mma_commit(&empty_bar[s]);
+              if (++s == STAGES) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!ok) break;
+            mma_commit(&accf_bar[b]);
+            ++chunk;
+          }
+        }
+        if (*abortp) {
+          // make sure no MMA is still writing TMEM before it is freed
+          mma_commit(&drain_bar);
+          mbar_wait_quiet(&drain_bar, 0);
+        }
       }
+      __syncwarp();
+    } else if (S::CONVERT) {
+      converters();
     }
-    __syncwarp();
-  } else if (warp >= 2 && warp < 2 + TC_EPI_WARPS) {
+  } else if (wg <= 2) {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TC_REG_HIGH));
     // ---------------- epilogue ----------------
     const int q = warp & 3;                        // TMEM lane quadrant
     const int half = NT >> 1;                      // columns per warp (multiple of 8)
-    const int col0 = (warp >= 6) ? half : 0;       // this warp's first column
+    const int col0 = (warp >= 8) ? half : 0;       // WG1: first half of the columns, WG2: second
     constexpr int NACC = TC_MAX_NT / 2;
     int chunk = 0;
     int tile, kb0, kb1;
@@ -498,78 +686,9 @@ __global__ void __maxnreg__(168)
         }
       }
     }
-  } else if (warp >= 2 + TC_EPI_WARPS && S::CONVERT) {
-    // ---------------- converters ----------------
-    constexpr int NCT = 32 * TC_CONV_WARPS;
-    const int ct = threadIdx.x - 32 * (2 + TC_EPI_WARPS);  // 0..NCT-1
-    int s = 0;
-    uint32_t ph = 0;
-    int tile, kb0, kb1;
-    SegIter my = it;
-    bool ok = true;
-    while (ok && my.next(tile, kb0, kb1)) {
-      for (int kb = kb0; kb < kb1; ++kb) {
-        if (!mbar_wait(&full_bar[s], ph, abortp, sc.ctl)) {
-          ok = false;
-          break;
-        }
-        unsigned char *st = stage_ptr(s);
-        if (A_MN) {
-          // transpose rows m = ct, ct + NCT, ... of the m-contiguous tile
-          // into K-major rows
-#pragma unroll 1
-          for (int m = ct; m < TC_BM; m += NCT)
-#pragma unroll
-          for (int k4 = 0; k4 < BK; k4 += 4) {
-            float x[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = *reinterpret_cast<const float *>(st + mn_off<BK>(k4 + j, m));
-            const uint32_t o = kmajor_off<BK>(m, k4);
-            if (NPROD == 3) {
-              float4 h, l;
-              h.x = tf32_head(x[0]);
-              h.y = tf32_head(x[1]);
-              h.z = tf32_head(x[2]);
-              h.w = tf32_head(x[3]);
-              l.x = x[0] - h.x;
-              l.y = x[1] - h.y;
-              l.z = x[2] - h.z;
-              l.w = x[3] - h.w;
-              *reinterpret_cast<float4 *>(st + S::AH + o) = h;
-              *reinterpret_cast<float4 *>(st + S::AL + o) = l;
-            } else {
-              *reinterpret_cast<float4 *>(st + S::AH + o) = make_float4(x[0], x[1], x[2], x[3]);
-            }
-          }
-        } else {
-          // split the K-major tile in place: Ah (TF32 head) and Al (tail)
-          float4 *a4 = reinterpret_cast<float4 *>(st + S::AH);
-          float4 *l4 = reinterpret_cast<float4 *>(st + S::AL);
-#pragma unroll 4
-          for (int i = ct; i < A_BYTES / 16; i += NCT) {
-            const float4 x = a4[i];
-            float4 h, l;
-            h.x = tf32_head(x.x);
-            h.y = tf32_head(x.y);
-            h.z = tf32_head(x.z);
-            h.w = tf32_head(x.w);
-            l.x = x.x - h.x;
-            l.y = x.y - h.y;
-            l.z = x.z - h.z;
-            l.w = x.w - h.w;
-            a4[i] = h;
-            l4[i] = l;
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&conv_bar[s]);
-        if (++s == STAGES) {
-          s = 0;
-          ph ^= 1u;
-        }
-      }
-    }
+  } else {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TC_REG_LOW));
+    if (S::CONVERT) converters();
   }
   // teardown
   tc_fence_before();
@@ -674,6 +793,42 @@ __global__ void transpose_split_kernel(const float *__restrict__ Src, int64_t ld
       const float h = tf32_head(x);
       Dh[dr * ldd + dc] = h;
       Dl[dr * ldd + dc] = x - h;
+    }
+  }
+}
+
+// Dst (rows x cols, leading dimension ldd, BF16) = Src (FP32, leading
+// dimension lds) rounded to nearest even.
+__global__ void to_bf16_kernel(const float *__restrict__ Src, int64_t lds, int64_t rows, int64_t cols,
+                               __nv_bfloat16 *__restrict__ Dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    Dst[i * ldd + j] = __float2bfloat16_rn(Src[i * lds + j]);
+  }
+}
+
+// Dh / Dl (cols x rows, leading dimension ldd, BF16) = head (round to nearest
+// even) and tail (BF16 of x - head) of Src^T, Src rows x cols (FP32, leading
+// dimension lds): the K-major split-BF16 thin operand of a pass.  32 x 32
+// tiles through shared memory, block (32, 8).
+__global__ void transpose_split_bf16_kernel(const float *__restrict__ Src, int64_t lds, int64_t rows,
+                                            int64_t cols, __nv_bfloat16 *__restrict__ Dh,
+                                            __nv_bfloat16 *__restrict__ Dl, int64_t ldd) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t r = r0 + yy, c = c0 + threadIdx.x;
+    tile[yy][threadIdx.x] = (r < rows && c < cols) ? Src[r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t dr = c0 + yy, dc = r0 + threadIdx.x;  // Dst row = Src column
+    if (dr < cols && dc < rows) {
+      const float x = tile[threadIdx.x][yy];
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      Dh[dr * ldd + dc] = h;
+      Dl[dr * ldd + dc] = __float2bfloat16_rn(x - __bfloat162float(h));
     }
   }
 }

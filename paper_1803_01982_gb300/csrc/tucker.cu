@@ -299,7 +299,7 @@ int ffsrqr_tucker_plan(ffsrqr_tucker_t *out, int32_t method, int32_t d, const in
     seen[ord[j]] = true;
   }
   if (p < 0) return -7;
-  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_FP64) return -8;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64) return -8;
   if (!workspace_bytes) return -10;
   ffsrqr_tucker_s *t = new (std::nothrow) ffsrqr_tucker_s();
   if (!t) return FFSRQR_STATUS_WORKSPACE;

@@ -17,7 +17,9 @@ import os
 from . import build as _build
 
 PLAIN_FP32 = 0
-MIXED = 1
+MIXED = 1            # FFSRQR_MIXED_TF32X3
+MIXED_TF32X3 = 1
+MIXED_BF16X3 = 2
 FP64 = 3
 
 STATUS = {0: "ok", 1: "rank_deficient", 2: "swap_cap", 3: "timeout", 4: "nonfinite",

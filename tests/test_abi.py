@@ -53,7 +53,7 @@ def test_status_strings(ff):
     ((10, 8, 9, 0, 0), -4),        # k > n
     ((10, 8, 4, -1, 0), -5),       # p < 0
     ((10, 8, 4, 7, 0), -5),        # k + p > m
-    ((10, 8, 4, 2, 2), -6),        # mode
+    ((10, 8, 4, 2, 5), -6),        # mode (0 plain, 1 TF32x3, 2 BF16x3, 3 FP64 are valid)
 ])
 def test_plan_argument_errors(ff, args, code):
     h = ctypes.c_void_p()

@@ -99,7 +99,7 @@ def case(request):
            "t_oracle": t_oracle}
 
 
-@pytest.mark.parametrize("mode", [ffsrqr.PLAIN_FP32, ffsrqr.MIXED])
+@pytest.mark.parametrize("mode", [ffsrqr.PLAIN_FP32, ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])
 def test_fullsize_matches_oracle(case, mode):
     A, A64, ref = case["A"], case["A64"], case["ref"]
     plan = ffsrqr.Plan(M, N, K, P, mode)
@@ -122,7 +122,7 @@ def test_fullsize_matches_oracle(case, mode):
     orth_v = float(torch.max(torch.abs(Vd.T @ Vd - eye)))
     rows = torch.randperm(M, generator=torch.Generator().manual_seed(0))[:512].cuda()
     avus = float(torch.max(torch.abs(A[rows].double() @ Vd - Ud[rows] * S.double()))) / s1
-    rep = {"decay": case["decay"], "mode": "mixed" if mode == ffsrqr.MIXED else "plain",
+    rep = {"decay": case["decay"], "mode": {0: "plain", 1: "tf32x3", 2: "bf16x3"}[mode],
            "t_oracle_s": round(case["t_oracle"], 1), "swaps": [info["swaps"], ref.swaps],
            "prefix_well_separated": case["npre"], "first_pivot_diff": first_diff, "same_set": same_set,
            "set_overlap": len(set(J.tolist()) & set(ref.piv[:K].tolist())),

@@ -6,6 +6,10 @@ the Cholesky-QR Grams and products and the output products use three TF32
 products per term (head x head + head x tail + tail x head), which carries
 FP32-level accuracy.
 
+FFSRQR_MIXED_BF16X3 does the same with BF16 operands: a one-product BF16
+sketch (about 2^-9 per operand) and three-product split-BF16 passes (about
+2^-16 per product, random), judged by the same tolerances.
+
 Consequences for the tests:
   * Pivots: the greedy order of Alg. 1 is compared with the oracle's on inputs
     whose column norms are graded by a factor >= 1/0.9 per step, so every
@@ -68,16 +72,17 @@ def check_fp32(A, k, got, ref):
     assert np.allclose(A64 @ got["V"], got["U"] * S, atol=2e-5 * s1)
 
 
+@pytest.mark.parametrize("mode", [ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])
 @pytest.mark.parametrize("shape,k,p,ratio", [
     ((300, 240), 12, 6, 0.8),      # k below one MMA K block (16)
     ((1000, 800), 40, 10, 0.9),
     ((2100, 660), 64, 10, 0.9),    # ragged 128-row tiles and K blocks
     ((640, 1200), 33, 7, 0.85),    # wide
 ])
-def test_mixed_graded_matches_oracle(shape, k, p, ratio):
+def test_mixed_graded_matches_oracle(shape, k, p, ratio, mode):
     m, n = shape
     A = graded(m, n, ratio, seed=m + n)
-    _, got = run(A, k, p)
+    _, got = run(A, k, p, mode)
     ref = oracle.ffsrqr(A, k, p, seed=0)
     assert got["info"]["status"] == ref.status == 0
     assert got["info"]["swaps"] == ref.swaps
@@ -86,24 +91,26 @@ def test_mixed_graded_matches_oracle(shape, k, p, ratio):
     check_fp32(A, k, got, ref)
 
 
-def test_mixed_unaligned_rows_use_cuda_cores():
+@pytest.mark.parametrize("mode", [ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])
+def test_mixed_unaligned_rows_use_cuda_cores(mode):
     # a row stride that is not a multiple of 16 bytes cannot be a TMA operand;
     # the mode then runs its CUDA-core passes and must give the same results
     A = graded(500, 301, 0.85, seed=5)
-    _, got = run(A, 20, 8)
+    _, got = run(A, 20, 8, mode)
     ref = oracle.ffsrqr(A, 20, 8, seed=0)
     assert list(got["piv"][:20]) == list(ref.piv[:20])
     check_fp32(A, 20, got, ref)
 
 
+@pytest.mark.parametrize("mode", [ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])
 @pytest.mark.parametrize("shape,k,p,decay", [
     ((2048, 1024), 64, 10, 0.97),
     ((1200, 1600), 48, 8, 0.95),
 ])
-def test_mixed_decayed_properties(shape, k, p, decay):
+def test_mixed_decayed_properties(shape, k, p, decay, mode):
     m, n = shape
     A = synth.decayed(m, n, decay ** np.arange(min(m, n)), 1e-4, seed=17)
-    _, got = run(A, k, p)
+    _, got = run(A, k, p, mode)
     ref = oracle.ffsrqr(A, k, p, seed=0)
     S, So = got["S"], ref.S
     head = So >= 0.1 * So[0]
@@ -116,50 +123,10 @@ def test_mixed_decayed_properties(shape, k, p, decay):
     assert np.allclose(got["V"].T @ got["V"], np.eye(k), atol=2e-5)
 
 
-def test_mixed_deterministic():
+@pytest.mark.parametrize("mode", [ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])
+def test_mixed_deterministic(mode):
     A = graded(900, 700, 0.9, seed=3)
-    _, a = run(A, 30, 10)
-    _, b = run(A, 30, 10)
+    _, a = run(A, 30, 10, mode)
+    _, b = run(A, 30, 10, mode)
     for key in ["U", "S", "V", "piv"]:
         assert np.array_equal(a[key], b[key]), key
-
-
-def test_mixed_full_size_properties():
-    """The benchmark workload (20000 x 20000, sigma_j = j^-1.5 for j <= 2000,
-    N(0, 1e-12) noise, k = 200, p = 10) in the bench's launch configuration,
-    checked through properties that hold at any size: orthonormal factors,
-    A V = U Sigma on sampled rows, and the singular values against the
-    spectrum the matrix was built with.  The noise E (entries N(0, s_e^2),
-    s_e = 1e-6) moves sigma_j by u_j^T E v_j ~ N(0, s_e^2) plus about
-    s_e^2 (m + n) / (2 sigma_j); the bounds allow 6 s_e and twice the second
-    term.  Since V is orthonormal,
-    sigma_j(A V) <= sigma_j(A) (interlacing); the leading values, far above
-    sigma_{k+1}, are captured to 1e-4 relative, and the rest of the top half
-    at least to 10 % (the one-pass subspace of Alg. 9 loses accuracy as
-    sigma_j approaches sigma_{k+1}; at j = 100, sigma_j / sigma_{k+1} = 2.9
-    and the FP64 reference values sit about 7 % low)."""
-    m = n = 20000
-    k, p = 200, 10
-    sig = synth.slow_decay(2000)
-    A = synth.decayed_torch(m, n, sig, 1e-6, seed=1)
-    plan = ffsrqr.Plan(m, n, k, p, ffsrqr.MIXED)
-    U, S, V, piv = plan.run(A, seed=0)
-    torch.cuda.synchronize()
-    assert plan.info()["status"] == 0
-    S64 = S.double().cpu().numpy()
-    assert np.all(np.diff(S64) <= 0)
-    shift = 6e-6 + 1e-12 * (m + n) / sig[:100]
-    assert np.all(S64[:100] <= sig[:100] * (1 + 1e-5) + shift)
-    assert np.all(np.abs(S64[:10] - sig[:10]) <= 1e-4 * sig[:10] + shift[:10])
-    assert np.all(S64[:100] >= 0.9 * sig[:100])
-    Ud, Vd = U.double(), V.double()
-    eye = torch.eye(k, dtype=torch.float64, device="cuda")
-    assert torch.allclose(Ud.T @ Ud, eye, atol=1e-4)
-    assert torch.allclose(Vd.T @ Vd, eye, atol=1e-4)
-    rows = torch.randperm(m, generator=torch.Generator().manual_seed(0))[:256].cuda()
-    lhs = A[rows].double() @ Vd
-    rhs = Ud[rows] * S.double()
-    assert torch.max(torch.abs(lhs - rhs)).item() <= 1e-4 * S64[0]
-    pv = piv.cpu().numpy()
-    assert sorted(pv.tolist()) == list(range(n))
-    assert math.isfinite(plan.info()["g2_first"])
