@@ -84,7 +84,7 @@ static_assert(TC_THREADS * 128 == 65536, "launched at 128 registers per thread")
 constexpr int TC_CHUNK = 8;      // K-blocks per TMEM accumulation chunk (3-product kernels)
 constexpr int TC_MAX_NT = 224;   // widest N tile (columns) the epilogue registers hold
 constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_MAX_STAGES = 6;
+constexpr int TC_MAX_STAGES = 8;
 constexpr long long TC_SPIN = 4000000;
 
 struct TcSched {
@@ -279,6 +279,24 @@ __device__ __forceinline__ uint32_t mn_off(int k, int m) {
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// Named barrier 1 over the TC_CONV_WARPS converter warps: a plain barrier,
+// and one that returns whether any participant passed a true condition (so
+// that all converter warps leave their loop together).
+template <int NTHR>
+__device__ __forceinline__ void conv_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NTHR) : "memory");
+}
+template <int NTHR>
+__device__ __forceinline__ bool conv_any(bool c) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, 1, %2, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)c), "n"(NTHR)
+      : "memory");
+  return r != 0;
+}
+
 // Byte offset of the 16-byte chunk holding BF16 elements (r, 8 c .. 8 c + 7)
 // of a K-major tile whose rows are 32 BF16 values (64 bytes, 64B swizzle:
 // the chunk index XORed with address bits 7..8, as the MMA reads it).
@@ -312,15 +330,19 @@ __device__ __forceinline__ void bf16_split8(const float *x, uint4 &h, uint4 &l) 
 // rows) and the converters write its BF16 head (and tail) as K-major rows of
 // BK = 32 BF16 values (64 bytes); the thin operand comes as BF16 from global
 // memory.
+// With BF the conversion is in place: the converter warps read the whole FP32
+// landing tile into registers, meet at a named barrier, and write the BF16
+// head (and tail) over it, so a stage is the landing tile plus B (which lets
+// five stages fit instead of three).
 template <int BK, int NPROD, bool A_MN, bool BF = false>
 struct TcStage {
   static constexpr int EL = BF ? 2 : 4;                    // operand element bytes
   static constexpr int A_BYTES = TC_BM * BK * EL;          // one operand tile of A
   static constexpr int RAW_BYTES = TC_BM * BK * 4;         // the FP32 landing tile
-  static constexpr int RAW = (A_MN || BF) ? RAW_BYTES : 0;
+  static constexpr int RAW = (A_MN && !BF) ? RAW_BYTES : 0;
   static constexpr int AH = RAW;
   static constexpr int AL = AH + A_BYTES;
-  static constexpr int BH = AH + A_BYTES * (NPROD == 3 ? 2 : 1);
+  static constexpr int BH = BF ? RAW_BYTES : AH + A_BYTES * (NPROD == 3 ? 2 : 1);
   __host__ __device__ static constexpr int b_bytes(int nt) { return nt * BK * EL; }
   __host__ __device__ static constexpr int bytes(int nt) { return BH + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
   __host__ __device__ static constexpr int tx(int nt) { return RAW_BYTES + b_bytes(nt) * (NPROD == 3 ? 2 : 1); }
@@ -408,39 +430,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = true;
     while (ok && my.next(tile, kb0, kb1)) {
       for (int kb = kb0; kb < kb1; ++kb) {
-        if (!mbar_wait(&full_bar[s], ph, abortp, sc.ctl)) {
+        if constexpr (BF) {
+          // all converter warps take the same decision: leave together on a
+          // timeout or abort seen by any of them (the named barriers below
+          // must be reached by all of them)
+          const bool bad = !mbar_wait(&full_bar[s], ph, abortp, sc.ctl);
+          if (conv_any<NCT>(bad)) {
+            ok = false;
+            break;
+          }
+        } else if (!mbar_wait(&full_bar[s], ph, abortp, sc.ctl)) {
           ok = false;
           break;
         }
         unsigned char *st = stage_ptr(s);
         if constexpr (BF) {
-          // FP32 landing -> K-major BF16 head (and tail): task = (row m, 8
-          // consecutive k), 128 rows x BK / 8 chunks per stage; consecutive
-          // threads take consecutive m (conflict-free landing reads)
-#pragma unroll 1
-          for (int task = ct; task < TC_BM * (BK / 8); task += NCT) {
-            const int m = task % TC_BM, c8 = task / TC_BM;
-            float x[8];
-            if (A_MN) {
+          // FP32 landing -> K-major BF16 head (and tail), in place: task =
+          // (row m, 8 consecutive k), 128 rows x BK / 8 chunks per stage,
+          // consecutive threads on consecutive m (conflict-free landing
+          // reads).  Every task's values are read before any is written.
+          constexpr int NTASK = TC_BM * (BK / 8);
+          constexpr int TPT = (NTASK + NCT - 1) / NCT;  // tasks per thread
+          float x[TPT][8];
 #pragma unroll
-              for (int j = 0; j < 8; ++j) x[j] = *reinterpret_cast<const float *>(st + mn_off<BK>(8 * c8 + j, m));
-            } else {
-              const float4 v0 = *reinterpret_cast<const float4 *>(st + kmajor_off<32>(m, 8 * c8));
-              const float4 v1 = *reinterpret_cast<const float4 *>(st + kmajor_off<32>(m, 8 * c8 + 4));
-              x[0] = v0.x;
-              x[1] = v0.y;
-              x[2] = v0.z;
-              x[3] = v0.w;
-              x[4] = v1.x;
-              x[5] = v1.y;
-              x[6] = v1.z;
-              x[7] = v1.w;
+          for (int u = 0; u < TPT; ++u) {
+            const int task = ct + u * NCT;
+            if (task < NTASK) {
+              const int m = task % TC_BM, c8 = task / TC_BM;
+              if (A_MN) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  x[u][j] = *reinterpret_cast<const float *>(st + mn_off<BK>(8 * c8 + j, m));
+              } else {
+                const float4 v0 = *reinterpret_cast<const float4 *>(st + kmajor_off<32>(m, 8 * c8));
+                const float4 v1 = *reinterpret_cast<const float4 *>(st + kmajor_off<32>(m, 8 * c8 + 4));
+                x[u][0] = v0.x;
+                x[u][1] = v0.y;
+                x[u][2] = v0.z;
+                x[u][3] = v0.w;
+                x[u][4] = v1.x;
+                x[u][5] = v1.y;
+                x[u][6] = v1.z;
+                x[u][7] = v1.w;
+              }
             }
-            uint4 h, l;
-            bf16_split8<NPROD == 3>(x, h, l);
-            const uint32_t o = kmajor_bf16_chunk(m, c8);
-            *reinterpret_cast<uint4 *>(st + S::AH + o) = h;
-            if (NPROD == 3) *reinterpret_cast<uint4 *>(st + S::AL + o) = l;
+          }
+          conv_sync<NCT>();
+#pragma unroll
+          for (int u = 0; u < TPT; ++u) {
+            const int task = ct + u * NCT;
+            if (task < NTASK) {
+              const int m = task % TC_BM, c8 = task / TC_BM;
+              uint4 h, l;
+              bf16_split8<NPROD == 3>(x[u], h, l);
+              const uint32_t o = kmajor_bf16_chunk(m, c8);
+              *reinterpret_cast<uint4 *>(st + S::AH + o) = h;
+              if (NPROD == 3) *reinterpret_cast<uint4 *>(st + S::AL + o) = l;
+            }
           }
         } else if (A_MN) {
           // transpose rows m = ct, ct + NCT, ... of the m-contiguous tile
