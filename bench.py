@@ -3,19 +3,19 @@
 
 Workload (default): A = U_r diag(sigma) V_r^T + E, m = n = 20000, r = 2000,
 sigma_j = j^-1.5 (slow decay), E ~ N(0, 1e-6^2), FP32, target rank k = 200,
-oversampling p = 10, FFSRQR_MIXED arithmetic.  A (1.6 GB) is larger than the
+oversampling p = 10, FFSRQR_MIXED_BF16X3 arithmetic.  A (1.6 GB) is larger than the
 129 MB L2, so no flush is needed between steps.  One step = one call of
 ffsrqr_run (all pipeline steps: sketch, QRCP, panel QR, R12 pass, SRQR test,
 QR of (R11 R12)^T, A Pi Qhat1 pass, small SVD, U and V).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the plain restatement of the
-paper's algorithm) on the host cores on the whole workload: one timed run of
-the same matrix (about two minutes on 16 cores at 20000 x 20000), no scaling;
-the line reports steps = 1, the runs that actually happened.  The cpu_baseline
-beside our own line is a bounded sample instead (the same recipe with a tenth
-of the columns, about 10-30 s), scaled to the workload by the operation count.
+The default line runs FFSRQR_MIXED_BF16X3; "modes" beside it times all three
+arithmetic modes (plain FP32, TF32x3, BF16x3) on the same matrix and states
+each one's singular-value and residual errors against the FP64 oracle run on
+the same array.  That oracle run (about 25 s on 16 host cores) is also the
+cpu_baseline: the whole workload, measured, no scaling.  --impl reference
+times the same oracle run on its own (one step: the runs that happened).
 With more than one GPU the replicas run independently (the method has no
 data-path exchange).  Prints one JSON line on rank 0.
 """
@@ -36,30 +36,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rank-k approx/s"
 UNIT = "approx/s"
-SAMPLE_COL_FRACTION = 10  # bounded CPU sample: the same rows, 1/10 of the columns
-
-
-def sample_shape(a):
-    """Shape of the bounded CPU sample: all m rows, n / 10 columns (at least
-    k + p, so the sample still has a rank-k problem)."""
-    return a.m, max(a.k + a.p + 1, a.n // SAMPLE_COL_FRACTION)
-
-
-def flops_model(m, n, k, s):
-    """Operation count used to scale CPU samples: the three products over A
-    (2mn(s + 2k), Sec. 3.2's 4mnl + 2(b+p)mn with l = b = k) plus the
-    Householder factorisations with explicit Q of the m x k panel, the m x k tmp
-    and the n x k (R11 R12)^T (8mk^2 + 4nk^2)."""
-    return 2.0 * m * n * (s + 2 * k) + 8.0 * m * k * k + 4.0 * n * k * k
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["mixed", "bf16x3", "plain"], default="mixed",
+    ap.add_argument("--mode", choices=["mixed", "bf16x3", "plain"], default="bf16x3",
                     help="mixed: TF32 sketch and three-product TF32 passes; bf16x3: BF16 sketch and "
                          "three-product split-BF16 passes; plain: FP32 on the CUDA cores")
     ap.add_argument("--decay", choices=["slow", "fast"], default="slow")
@@ -68,7 +51,9 @@ def parse():
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=24)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the FP64 oracle run (cpu_baseline and the modes' errors against it)")
+    ap.add_argument("--no-modes", action="store_true", help="skip the comparison of the three modes")
     ap.add_argument("--workload", choices=["single", "batch", "hosvd", "sthosvd", "hosvd-core", "rpca", "rsisvd",
                                            "serving"],
                     default="single",
@@ -93,27 +78,8 @@ def spectrum(a, r):
 
 
 # --------------------------------------------------------------------------
-# CPU oracle sample
+# CPU oracle baselines of the other workloads
 # --------------------------------------------------------------------------
-def oracle_sample(a, reps=1):
-    import numpy as np
-
-    import oracle
-    from paper_1803_01982_gb300 import synth
-    oracle.build()
-    sm, sn = sample_shape(a)
-    r = min(2000, sm, sn)
-    A = synth.decayed(sm, sn, spectrum(a, r), 1e-6, seed=1, dtype=np.float32)
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.ffsrqr(A, a.k, a.p, seed=0)
-        times.append(time.perf_counter() - t0)
-    s = a.k + a.p
-    scale = flops_model(sm, sn, a.k, s) / flops_model(a.m, a.n, a.k, s)
-    return times, scale
-
-
 def tucker_cpu_baseline(X_host, ranks, st_method: bool):
     """The FP64 oracle's Tucker decomposition of the same tensor on the host
     cores: (seconds, sample text).  Only the benchmark calls it."""
@@ -149,13 +115,6 @@ def rpca_cpu_baseline(m_full: int):
 def cores_used():
     env = os.environ.get("OMP_NUM_THREADS")
     return int(env) if env else (os.cpu_count() or 1)
-
-
-def sample_text(a):
-    sm, sn = sample_shape(a)
-    return (f"FP64 oracle on a {sm}x{sn} matrix of the same recipe (k={a.k}, p={a.p}), one run; "
-            f"time scaled to {a.m}x{a.n} by the operation-count model "
-            "2mn(s+2k) + 8mk^2 + 4nk^2")
 
 
 # --------------------------------------------------------------------------
@@ -380,11 +339,17 @@ def run_ours(a, rank, world, local_rank):
         e2e = {"value": world * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 4,
                "d2h_bytes_per_step": d2h, "ms_per_step": ems}
 
-    cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu:
-        times, scale = oracle_sample(a, reps=1)
-        cpu = {"value": scale / times[0], "unit": UNIT, "cores": cores_used(), "kind": "oracle",
-               "sample": sample_text(a), "sample_seconds": times[0]}
+    # the three arithmetic modes on the same matrix (a few steps each) and
+    # their errors against the FP64 oracle run on the same array, which is
+    # also the CPU baseline (the whole workload, about 25 s on 16 cores)
+    modes, cpu = None, None
+    if rank == 0 and world == 1:
+        modes = compare_modes(a, A, dev) if not a.no_modes else None
+        if not a.no_cpu:
+            cpu, ref = oracle_full(a, A)
+            if modes:
+                mode_errors(a, A, modes, ref)
+            cpu.pop("ref", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -393,9 +358,97 @@ def run_ours(a, rank, world, local_rank):
                 "roofline": roof,
                 "three_pass_roofline": {"ms": three_pass_ms, "frac_of_step": three_pass_ms / ms},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * a.steps,
+                "modes": {k: {kk: vv for kk, vv in v.items() if kk != "out"} for k, v in modes.items()}
+                if modes else None,
                 "clocks": clocks, "phases_ms": {k: round(v, 4) for k, v in phases.items()},
                 "status": info["status"], "swaps": info["swaps"], "g2": info["g2_first"]}
         print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the three modes side by side, with their errors against the FP64 oracle
+# --------------------------------------------------------------------------
+MODE_IDS = {"plain": 0, "mixed": 1, "bf16x3": 2}
+
+
+def compare_modes(a, A, dev, steps=3, warm=2):
+    """Each arithmetic mode on the same device matrix: ms per step (CUDA
+    events over `steps` back-to-back runs after `warm` warm-up runs) and the
+    outputs of one run (kept for mode_errors)."""
+    import torch
+
+    from paper_1803_01982_gb300 import ffsrqr
+    out = {}
+    for name, mid in MODE_IDS.items():
+        plan = ffsrqr.Plan(a.m, a.n, a.k, a.p, mid, device=dev)
+        res = plan.outputs()
+        for _ in range(warm):
+            plan.run(A, 0, res)
+        torch.cuda.synchronize(dev)
+        st = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            plan.run(A, 0, res)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "value": 1000.0 / ms, "status": plan.info()["status"],
+                     "out": [t.clone() for t in res]}
+        del plan
+    return out
+
+
+def residual_fro_device(A, U, S, V, rows=2048):
+    """||A - U diag(S) V^T||_F in FP64 on the device, by row blocks
+    (measurement arithmetic, not the factorisation path)."""
+    import torch
+    U, S, V = U.double(), S.double(), V.double()
+    US = U * S
+    tot = 0.0
+    for r0 in range(0, A.shape[0], rows):
+        blk = A[r0:r0 + rows].double() - US[r0:r0 + rows] @ V.T
+        tot += float((blk * blk).sum())
+    return tot ** 0.5
+
+
+def oracle_full(a, A):
+    """The FP64 oracle on the same array (upcast), timed on the host cores:
+    the CPU baseline on the whole workload, no scaling."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    A64 = A.cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    ref = oracle.ffsrqr(A64, a.k, a.p, seed=0)
+    dt = time.perf_counter() - t0
+    del A64
+    cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+           "sample": f"the whole workload ({a.m}x{a.n}, k={a.k}, p={a.p}), one run on the same array, no scaling",
+           "seconds": dt}
+    return cpu, ref
+
+
+def mode_errors(a, A, modes, ref):
+    """Each mode's singular values and Frobenius residual against the FP64
+    oracle's (relative), and how much of its column set it shares."""
+    import numpy as np
+    import torch
+    So = ref.S
+    head = So >= 0.1 * So[0]
+    Ud, Sd, Vd = (torch.from_numpy(x).to(A.device) for x in (ref.U, ref.S, ref.V))
+    res_o = residual_fro_device(A, Ud, Sd, Vd)
+    for name, m in modes.items():
+        U, S, V, piv = m.pop("out")
+        Sg = S.double().cpu().numpy()
+        rel = np.abs(Sg - So) / So
+        res = residual_fro_device(A, U, S, V)
+        J = set(piv[:a.k].cpu().numpy().tolist())
+        m.update({"sigma_rel_err_head_max": float(rel[head].max()), "sigma_rel_err_max": float(rel.max()),
+                  "residual_rel_err": (res - res_o) / res_o,
+                  "pivot_set_shared": len(J & set(ref.piv[:a.k].tolist())) / a.k})
+    return modes
 
 
 # --------------------------------------------------------------------------
