@@ -1082,7 +1082,7 @@ void layout(ffsrqr_plan_s *P) {
   P->off_bt = take((size_t)n * lds * E);
   P->off_sel = take((size_t)n * sizeof(int));
   P->off_s11 = take((size_t)k * k * E);
-  P->off_cval = take((size_t)2 * P->qrcp_grid * E);
+  P->off_cval = take((size_t)4 * P->qrcp_grid * E);  // [2][2][G]: bests and bounds
   P->off_cidx = take((size_t)2 * P->qrcp_grid * sizeof(int));
   P->off_ccol = take((size_t)2 * P->qrcp_grid * lds * E);
   P->off_q1 = take((size_t)m * ldk * E);
@@ -1238,7 +1238,10 @@ int plan_qrcp(ffsrqr_plan_s *P) {
   int64_t grid = std::min<int64_t>(P->num_sms, std::max<int64_t>(1, cdiv(P->n, 16)));
   for (;;) {
     const int64_t cols = cdiv(P->n, grid);
-    const size_t need = ((size_t)cols * P->qrcp_spad + cols + P->qrcp_spad) * sizeof(T);
+    // slab, reflector, norms; single precision adds the second reflector and
+    // the candidate columns of the two-pivot steps (16-byte aligned)
+    const size_t need = ((size_t)cols * P->qrcp_spad + cols + P->qrcp_spad) * sizeof(T) +
+                        (sizeof(T) == 4 ? (size_t)qrcp_pair_extra(P->qrcp_spad) * sizeof(T) + 16 : 0);
     if (need <= budget) {
       P->qrcp_cols = (int)cols;
       P->qrcp_smem = need;

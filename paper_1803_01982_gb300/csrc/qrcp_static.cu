@@ -36,10 +36,10 @@ constexpr int64_t QS_MAX_LDS = 256;  // leading dimension of B^T (>= s)
 constexpr int QS_MAX_GRID = 256;     // blocks of the cooperative QRCP
 constexpr size_t QS_CTL = 256;       // CTL_WORDS control words, zeroed per call
 constexpr size_t QS_CVAL = QS_CTL;
-constexpr size_t QS_CIDX = QS_CVAL + sizeof(float) * 2 * QS_MAX_GRID;
+constexpr size_t QS_CIDX = QS_CVAL + sizeof(float) * 4 * QS_MAX_GRID;  // bests and bounds, two buffers
 constexpr size_t QS_CCOL = QS_CIDX + sizeof(int) * 2 * QS_MAX_GRID;
 constexpr size_t QS_SEL = QS_CCOL + sizeof(float) * 2 * QS_MAX_GRID * QS_MAX_LDS;
-constexpr size_t QS_BYTES = QS_SEL + sizeof(int) * QS_MAX_N;  // 790,784 bytes
+constexpr size_t QS_BYTES = QS_SEL + sizeof(int) * QS_MAX_N;  // 792,832 bytes
 static_assert(QS_CTL >= CTL_WORDS * sizeof(int), "control words");
 
 static __device__ __align__(256) unsigned char g_qrcp_scratch[QS_BYTES];
@@ -91,7 +91,7 @@ extern "C" int ffsrqr_qrcp_static(const float *Bt, int64_t n, int32_t s, int64_t
   size_t smem = 0;
   for (;;) {
     cols = (int)cdiv(n, grid);
-    smem = ((size_t)cols * spad + cols + spad) * sizeof(float);
+    smem = ((size_t)cols * spad + cols + spad + qrcp_pair_extra(spad)) * sizeof(float) + 16;
     if (smem + 2048 <= (size_t)optin) break;
     if (grid >= gmax) return FFSRQR_STATUS_UNSUPPORTED;
     grid = std::min<int64_t>(gmax, grid * 2);
