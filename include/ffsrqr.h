@@ -178,7 +178,10 @@ const char *ffsrqr_last_cuda_error(void);
  * step-by-step checks.  what: 0 Omega (s x m), 1 B^T (n x s), 2 S11 (k x k,
  * R factor of the sketched pivot columns), 3 Q1 (m x k), 4 G^T = A^T Q1
  * (n x k, original column order), 5 V' = Pi Qhat1 (n x k), 6 tmp = A V'
- * (m x k), 7 trailing estimates r (n), 8 M_t (k x k, tmp = Q_t M_t).
+ * (m x k), 7 trailing estimates r (n), 8 M_t (k x k, tmp = Q_t M_t), 9 the
+ * device control words (1 x 40 int32: status, counters; words 14 and 15
+ * count the second Cholesky-QR sweeps that took the first-order expansion of
+ * their factor and the exact factorization).
  * Writes the byte offset, row/column counts and leading dimension (elements)
  * and the element size in bytes.  Returns 0 or -2 for an unknown item. */
 int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,

@@ -23,6 +23,9 @@ enum CtlSlot : int {
   CTL_BARRIER2 = 10,
   CTL_JACOBI_SWEEPS = 11,
   CTL_NONFINITE = 12,
+  CTL_SERIES_SKIP = 13,   // 1 while the current second Cholesky-QR factor came from the expansion
+  CTL_SERIES = 14,        // second Cholesky-QR sweeps that took the first-order expansion
+  CTL_SERIES_EXACT = 15,  // second sweeps that took the exact factorization
   CTL_SWEEP_ROT0 = 16,  // rotations performed in Jacobi sweeps 0..15 (diagnostic)
   CTL_WIN_KEY = 32,     // 3 x uint64 (words 32..37): QRCP winner keys, one per step mod 3
   CTL_WORDS = 40,

@@ -30,6 +30,7 @@
 
 #include "../../include/ffsrqr.h"
 #include "common.cuh"
+#include "chol_inv.cuh"
 #include "dense_small.cuh"
 #include "gemm_simt.cuh"
 #include "jacobi.cuh"
@@ -117,7 +118,7 @@ struct ffsrqr_plan_s {
   int nblk_tn;  // blocks of the trailing-norm kernel
   int nblk_res; // blocks of the SRQR residual kernels
   int nblk_sign;
-  Item items[9];
+  Item items[10];
   // phase events (FFSRQR_FLAG_PHASE_TIMES), two sets used by alternate runs
   // so that a run's times can be read while the next run executes
   cudaEvent_t ev[2][13];
@@ -136,6 +137,10 @@ struct ffsrqr_plan_s {
 namespace {
 
 constexpr long long kSpinLimit = 2000000;  // ~1 s of polling (each poll is an L2 round trip + 20 ns sleep)
+// Largest ||X1^T X1 - I||_F for which the second Cholesky-QR sweep uses the
+// first-order expansion of its factor: the dropped terms leave
+// ||Q^T Q - I|| <= 3 ||E||^2 <= 3e-6.
+constexpr float kSeriesTol = 1e-3f;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -558,18 +563,27 @@ int tc_gram(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const fl
   return launch_tc(st, P, ws, -1, 3, true, k, k, (int)rows, X, ldx, b.bh, b.bl, ldt, W, k);
 }
 
-// sh / sl = split of (R^{-1})^T for an upper-triangular R (k x k, ld k): the
-// K-major operand of the product X R^{-1}.  The inverse is formed by the
-// row-wise triangular solve on the identity.
-int tc_inv_t(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const float *R) {
+// R (upper triangular, k x k) = chol(W) and sh / sl = split of (R^{-1})^T,
+// the K-major operand of the product X R^{-1}, in one launch.
+// second: W is the Gram of a first sweep's output (I + E); if ||E||_F is
+// small the factor comes from its first-order expansion (cholqr_series_kernel)
+// and the exact kernel returns at once.
+int tc_chol_inv(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const float *W, float *R,
+                bool second = false) {
   const int k = P->k;
+  if (k > 256) return FFSRQR_STATUS_UNSUPPORTED;
   const TcBufs b = tc_bufs(P, ws);
-  int rc;
-  eye_kernel<float><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(b.sinv, k, P->ldk);
-  CKL("eye");
-  if ((rc = launch_trsm<float, false>(st, P, b.sinv, P->ldk, k, R, 1, k))) return rc;
-  split_tf32_kernel<<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(b.sinv, P->ldk, k, k, b.sh, b.sl);
-  CKL("split_tf32");
+  int *ctl = reinterpret_cast<int *>(ws + P->off_ctl);
+  const int *skip = nullptr;
+  if (second) {
+    cholqr_series_kernel<<<1, CS_THREADS, 0, st>>>(W, k, kSeriesTol, R, b.sh, b.sl, P->ldk, ctl,
+                                                   ctl + CTL_SERIES_SKIP);
+    CKL("cholqr_series");
+    skip = ctl + CTL_SERIES_SKIP;
+  }
+  CK(smem_cap_max((const void *)chol_inv_kernel));
+  chol_inv_kernel<<<1, CI_THREADS, chol_inv_smem(k), st>>>(W, k, R, b.sh, b.sl, P->ldk, ctl, skip);
+  CKL("chol_inv");
   return 0;
 }
 
@@ -594,15 +608,12 @@ int cholqr2_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, const
   float *W = reinterpret_cast<float *>(ws + P->off_w);
   float *R1 = reinterpret_cast<float *>(ws + P->off_rc1);
   float *R2 = reinterpret_cast<float *>(ws + P->off_rc2);
-  int *ctl = reinterpret_cast<int *>(ws + P->off_ctl);
   int rc;
   if ((rc = tc_gram(st, P, ws, X, ldk, rows, W))) return rc;
-  if ((rc = launch_chol<float>(st, P, W, R1, ctl))) return rc;
-  if ((rc = tc_inv_t(st, P, ws, R1))) return rc;
+  if ((rc = tc_chol_inv(st, P, ws, W, R1))) return rc;
   if ((rc = tc_mul(st, P, ws, X, ldk, rows, k, k, b.scr, ldk))) return rc;
   if ((rc = tc_gram(st, P, ws, b.scr, ldk, rows, W))) return rc;
-  if ((rc = launch_chol<float>(st, P, W, R2, ctl))) return rc;
-  if ((rc = tc_inv_t(st, P, ws, R2))) return rc;
+  if ((rc = tc_chol_inv(st, P, ws, W, R2, true))) return rc;
   if ((rc = tc_mul(st, P, ws, b.scr, ldk, rows, k, k, Q, ldk))) return rc;
   if (Rout) {
     trmm_upper_kernel<float><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(R2, R1, k, Rout);
@@ -1170,6 +1181,11 @@ void layout(ffsrqr_plan_s *P) {
   item(6, P->off_tmp, m, k, ldk);
   item(7, P->off_r, n, 1, 1);
   item(8, P->off_mt, k, k, k);
+  P->items[9].off = P->off_ctl;  // the control words (int32)
+  P->items[9].rows = 1;
+  P->items[9].cols = CTL_WORDS;
+  P->items[9].ld = CTL_WORDS;
+  P->items[9].elem = 4;
 }
 
 // The QR kernels of the small SVD and the shape of the Jacobi cluster: the
@@ -1580,7 +1596,7 @@ int ffsrqr_launch_count(ffsrqr_plan_t plan) {
 int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,
                           int64_t *cols, int64_t *ld, int32_t *elem_bytes) {
   if (!plan) return -1;
-  if (what < 0 || what > 8) return -2;
+  if (what < 0 || what > 9) return -2;
   const Item &it = plan->items[what];
   if (offset) *offset = it.off;
   if (rows) *rows = it.rows;

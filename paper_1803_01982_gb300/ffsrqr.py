@@ -25,7 +25,7 @@ FP64 = 3
 STATUS = {0: "ok", 1: "rank_deficient", 2: "swap_cap", 3: "timeout", 4: "nonfinite",
           5: "workspace", 6: "cuda", 7: "unsupported"}
 
-ITEM = {"omega": 0, "bt": 1, "s11": 2, "q1": 3, "gt": 4, "vp": 5, "tmp": 6, "r": 7, "mt": 8}
+ITEM = {"omega": 0, "bt": 1, "s11": 2, "q1": 3, "gt": 4, "vp": 5, "tmp": 6, "r": 7, "mt": 8, "ctl": 9}
 
 
 class Opts(ctypes.Structure):
@@ -313,7 +313,7 @@ class Plan:
         _check(lib.ffsrqr_workspace_item(self._h, ITEM[name], ctypes.byref(off), ctypes.byref(r),
                                          ctypes.byref(c), ctypes.byref(ld), ctypes.byref(eb)),
                "ffsrqr_workspace_item")
-        dt = torch.float64 if eb.value == 8 else torch.float32
+        dt = torch.float64 if eb.value == 8 else (torch.int32 if name == "ctl" else torch.float32)
         start = self._ws_off + off.value
         nbytes = (r.value - 1) * ld.value * eb.value + c.value * eb.value
         raw = self.workspace[start:start + nbytes]

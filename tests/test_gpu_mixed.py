@@ -54,7 +54,8 @@ def run(A, k, p, mode=ffsrqr.MIXED, seed=0):
     U, S, V, piv = plan.run(Ad, seed=seed)
     torch.cuda.synchronize()
     return plan, {"U": U.double().cpu().numpy(), "S": S.double().cpu().numpy(),
-                  "V": V.double().cpu().numpy(), "piv": piv.cpu().numpy(), "info": plan.info()}
+                  "V": V.double().cpu().numpy(), "piv": piv.cpu().numpy(), "info": plan.info(),
+                  "ctl": plan.item("ctl")[0].cpu().numpy()}
 
 
 def check_fp32(A, k, got, ref):
@@ -89,6 +90,10 @@ def test_mixed_graded_matches_oracle(shape, k, p, ratio, mode):
     assert list(got["piv"][:k]) == list(ref.piv[:k])
     assert got["info"]["g2_first"] == pytest.approx(ref.g2_first, rel=1e-3)
     check_fp32(A, k, got, ref)
+    # the three preconditioned QRs (panel, Z^T, Y_t) are well conditioned, so
+    # each second Cholesky-QR sweep takes the first-order expansion
+    ctl = got["ctl"]
+    assert ctl[14] == 3 and ctl[15] == 0, ctl[13:16]
 
 
 @pytest.mark.parametrize("mode", [ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])

@@ -50,6 +50,23 @@ def test_fp32_matches_oracle(mode, shape, k, p, q):
     assert np.allclose(A64.T @ U, V * S, atol=2e-5 * s1)
 
 
+def test_second_cholqr_sweep_falls_back_to_exact_factor():
+    # sigma_j = 0.9^j and k + p = 50: the QRs here are not preconditioned and
+    # their first sweeps leave ||Q^T Q - I|| of order cond^2 u ~ 1e-3 or more
+    # (cond(A Omega) ~ 0.9^-50), above the expansion's limit, so second sweeps
+    # factor their Grams exactly; the results must still match the oracle
+    m, n, k, p, q = 1000, 800, 40, 10, 1
+    A = synth.decayed(m, n, 0.9 ** np.arange(min(m, n)), 1e-4, seed=9)
+    pl, U, S, V = run(A, k, p, q, ffsrqr.MIXED)
+    ctl = pl.item("ctl")[0].cpu().numpy()
+    # QRs: A Omega, then A^T Q and A Q per iteration, then the last A^T Q
+    assert ctl[15] >= 1 and ctl[14] + ctl[15] == 2 + 2 * q, ctl[13:16]
+    Uo, So, Vo = ors.rsisvd(A, k, p, q)
+    s1 = So[0]
+    assert np.all(np.abs(S - So) <= 2e-5 * s1 + 1e-5 * So)
+    assert np.allclose(U.T @ U, np.eye(k), atol=2e-5) and np.allclose(V.T @ V, np.eye(k), atol=2e-5)
+
+
 def test_plan_arguments():
     import ctypes
     h = ctypes.c_void_p()
