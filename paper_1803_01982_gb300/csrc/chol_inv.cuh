@@ -267,10 +267,14 @@ __global__ void __launch_bounds__(CI_THREADS, 1)
 // = I + O(||E||^2), since U + U^T = E.  So when ||E||_F <= tol the kernel
 // writes R = I + U and the split of M^T (the operand of X1 M) and sets *skip,
 // and the exact chol_inv_kernel launched after it returns at once; otherwise
-// it leaves both to chol_inv_kernel.  One CTA of CS_THREADS threads.
+// it leaves both to chol_inv_kernel.  Every CTA computes ||E||_F over all of
+// W in the same order (so all take the same decision) and writes its own
+// CS_THREADS entries; block 0 records the decision.
 // Counters: ctl[CTL_SERIES] / ctl[CTL_SERIES_EXACT] count the sweeps that took
 // the expansion / the exact factorization.
 constexpr int CS_THREADS = 1024;
+
+inline int cholqr_series_grid(int k) { return (k * k + CS_THREADS - 1) / CS_THREADS; }
 
 __global__ void __launch_bounds__(CS_THREADS, 1)
     cholqr_series_kernel(const float *__restrict__ W, int k, float tol, float *__restrict__ R,
@@ -293,13 +297,16 @@ __global__ void __launch_bounds__(CS_THREADS, 1)
     if (tid == 0) {
       const int use = (t <= tol * tol) ? 1 : 0;  // false for a NaN
       s_use = use;
-      *skip = use;
-      atomicAdd(ctl + (use ? CTL_SERIES : CTL_SERIES_EXACT), 1);
+      if (blockIdx.x == 0) {
+        *skip = use;
+        atomicAdd(ctl + (use ? CTL_SERIES : CTL_SERIES_EXACT), 1);
+      }
     }
   }
   __syncthreads();
   if (!s_use) return;
-  for (int e = tid; e < k * k; e += CS_THREADS) {
+  const int e = blockIdx.x * CS_THREADS + tid;
+  if (e < k * k) {
     const int i = e / k, j = e - i * k;
     // U(i, j) for i <= j (upper triangle); W's upper triangle is read
     const float u = (i < j) ? W[e] : ((i == j) ? 0.5f * (W[e] - 1.f) : 0.f);

@@ -15,12 +15,33 @@ namespace ffq {
 template <typename T>
 __global__ void gather_cols_kernel(const T *__restrict__ A, int64_t lda, int64_t m, int k,
                                    const int32_t *__restrict__ piv, T *__restrict__ P, int64_t ldp) {
-  const int64_t total = m * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / k;
-    const int j = (int)(e - i * k);
-    P[i * ldp + j] = A[i * lda + piv[j]];
+  // a warp per row; lane l copies columns l, l + 32, ... of the row, with the
+  // pivot indices held in registers, so each lane has up to 8 independent
+  // (scattered) loads in flight
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int j0 = 0; j0 < k; j0 += 256) {
+    int pj[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + lane + 32 * u;
+      pj[u] = (j < k) ? piv[j] : 0;
+    }
+    for (int64_t i = w0; i < m; i += nw) {
+      const T *a = A + i * lda;
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + lane + 32 * u;
+        if (j < k) v[u] = a[pj[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + lane + 32 * u;
+        if (j < k) P[i * ldp + j] = v[u];
+      }
+    }
   }
 }
 
@@ -671,25 +692,41 @@ __global__ void srqr_g2_kernel(const T *__restrict__ npart, int nnp, const T *__
 // piv[k:n] = columns not in J, ascending (one block, chunked scan).
 __global__ void __launch_bounds__(1024) piv_rest_kernel(const int *__restrict__ sel, int64_t n, int k,
                                                         int32_t *__restrict__ piv) {
-  __shared__ int counts[1024];
-  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t i0 = threadIdx.x * chunk, i1 = min(n, i0 + chunk);
-  int cnt = 0;
-  for (int64_t i = i0; i < i1; ++i) cnt += (sel[i] == 0);
-  counts[threadIdx.x] = cnt;
+  // tiles of blockDim.x consecutive columns; a block-wide exclusive scan of
+  // the "not selected" flags gives each unselected column its position
+  __shared__ int wsum[32];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_base = k;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      const int c = counts[t];
-      counts[t] = acc;
-      acc += c;
+  for (int64_t t0 = 0; t0 < n; t0 += blockDim.x) {
+    const int64_t i = t0 + threadIdx.x;
+    const int f = (i < n && sel[i] == 0) ? 1 : 0;
+    int x = f;  // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int z = (lane < nw) ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      if (lane < nw) wsum[lane] = z;  // inclusive over warps
+    }
+    __syncthreads();
+    const int base = s_base;
+    const int pos = base + (w > 0 ? wsum[w - 1] : 0) + x - f;
+    if (f && pos < n) piv[pos] = (int32_t)i;
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = base + wsum[nw - 1];
+    __syncthreads();
   }
-  __syncthreads();
-  int pos = k + counts[threadIdx.x];
-  for (int64_t i = i0; i < i1; ++i)
-    if (sel[i] == 0 && pos < n) piv[pos++] = (int32_t)i;
 }
 
 // Sign rule, stage 1: for each column j of U (m x k), the row of the
@@ -703,7 +740,20 @@ __global__ void __launch_bounds__(256) sign_partial_kernel(const T *__restrict__
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     T bv = T(-1);
     int bi = 0x7fffffff;
-    for (int64_t i = i0; i < i1; ++i) {
+    int64_t i = i0;
+    // four rows' loads in flight, compared in row order
+    for (; i + 4 <= i1; i += 4) {
+      T a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = fabs(U[(i + u) * ldu + j]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (a[u] > bv) {
+          bv = a[u];
+          bi = (int)(i + u);
+        }
+    }
+    for (; i < i1; ++i) {
       const T a = fabs(U[i * ldu + j]);
       if (a > bv) {
         bv = a;
@@ -719,10 +769,14 @@ __global__ void __launch_bounds__(256) sign_partial_kernel(const T *__restrict__
 template <typename T>
 __global__ void sign_final_kernel(const T *__restrict__ U, int64_t ldu, int k, const T *__restrict__ pv,
                                   const int *__restrict__ pi, int nparts, T *__restrict__ sgn) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+  // a warp per column: lanes scan the parts, then a warp reduction; the
+  // winner is the largest value, ties to the lowest row (an order-free rule)
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < k; j += nw) {
     T bv = T(-1);
     int bi = 0x7fffffff;
-    for (int b = 0; b < nparts; ++b) {
+    for (int b = lane; b < nparts; b += 32) {
       const T v = pv[(int64_t)b * k + j];
       const int i = pi[(int64_t)b * k + j];
       if (i != 0x7fffffff && (v > bv || (v == bv && i < bi))) {
@@ -730,7 +784,16 @@ __global__ void sign_final_kernel(const T *__restrict__ U, int64_t ldu, int k, c
         bi = i;
       }
     }
-    sgn[j] = (bi != 0x7fffffff && U[(int64_t)bi * ldu + j] < T(0)) ? T(-1) : T(1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi != 0x7fffffff && (ov > bv || (ov == bv && oi < bi))) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) sgn[j] = (bi != 0x7fffffff && U[(int64_t)bi * ldu + j] < T(0)) ? T(-1) : T(1);
   }
 }
 
@@ -738,13 +801,11 @@ __global__ void sign_final_kernel(const T *__restrict__ U, int64_t ldu, int k, c
 template <typename T>
 __global__ void scale_cols_kernel(T *__restrict__ X, int64_t ldx, int64_t rows, int k,
                                   const T *__restrict__ sgn) {
-  const int64_t total = rows * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / k;
-    const int j = (int)(e - i * k);
-    X[i * ldx + j] *= sgn[j];
-  }
+  // a warp per row, lanes along the row
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < rows; i += nw)
+    for (int j = lane; j < k; j += 32) X[i * ldx + j] *= sgn[j];
 }
 
 // Copy a rows x cols block between leading dimensions.
@@ -752,12 +813,11 @@ template <typename T>
 __global__ void copy2d_kernel(const T *__restrict__ Src, int64_t lds, T *__restrict__ Dst, int64_t ldd,
                               int64_t rows, int64_t cols, const int *gate) {
   if (gate && *gate == 0) return;
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / cols, j = e - i * cols;
-    Dst[i * ldd + j] = Src[i * lds + j];
-  }
+  // a warp per row, lanes along the row
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < rows; i += nw)
+    for (int64_t j = lane; j < cols; j += 32) Dst[i * ldd + j] = Src[i * lds + j];
 }
 
 // Control-word defaults: g2 = 1 (no test possible when k = n), no candidate.

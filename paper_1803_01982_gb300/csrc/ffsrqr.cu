@@ -576,7 +576,7 @@ int tc_chol_inv(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, cons
   int *ctl = reinterpret_cast<int *>(ws + P->off_ctl);
   const int *skip = nullptr;
   if (second) {
-    cholqr_series_kernel<<<1, CS_THREADS, 0, st>>>(W, k, kSeriesTol, R, b.sh, b.sl, P->ldk, ctl,
+    cholqr_series_kernel<<<cholqr_series_grid(k), CS_THREADS, 0, st>>>(W, k, kSeriesTol, R, b.sh, b.sl, P->ldk, ctl,
                                                    ctl + CTL_SERIES_SKIP);
     CKL("cholqr_series");
     skip = ctl + CTL_SERIES_SKIP;
@@ -923,7 +923,7 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   }
   sign_partial_kernel<T><<<P->nblk_sign, 256, 0, st>>>(U, ldu, m, k, w.sgnv, w.sgni);
   CKL("sign_partial");
-  sign_final_kernel<T><<<(unsigned)cdiv(k, 256), 256, 0, st>>>(U, ldu, k, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
+  sign_final_kernel<T><<<(unsigned)cdiv((int64_t)k * 32, 256), 256, 0, st>>>(U, ldu, k, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
   CKL("sign_final");
   scale_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * k, 256), 8 * nsm), 256, 0, st>>>(U, ldu, m, k,
                                                                                               w.sgn);
@@ -1050,7 +1050,7 @@ int run_rsi(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int6
   }
   sign_partial_kernel<T><<<P->nblk_sign, 256, 0, st>>>(uo, lduo, m, l, w.sgnv, w.sgni);
   CKL("sign_partial");
-  sign_final_kernel<T><<<(unsigned)cdiv(l, 256), 256, 0, st>>>(uo, lduo, l, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
+  sign_final_kernel<T><<<(unsigned)cdiv((int64_t)l * 32, 256), 256, 0, st>>>(uo, lduo, l, w.sgnv, w.sgni, P->nblk_sign, w.sgn);
   CKL("sign_final");
   scale_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * l, 256), 8 * nsm), 256, 0, st>>>(uo, lduo, m, l,
                                                                                               w.sgn);

@@ -22,11 +22,14 @@
 //      inner round r pairing column q of slot 0 with column (q + r) mod b of
 //      slot 1.  Pair slot q keeps column q of slot 0 in registers for the
 //      whole outer round; the slot-1 columns stay in shared memory.
-//   Between outer rounds each block pulls its two blocks of the next round
-//   from the blocks that hold them (distributed shared memory), into its
-//   second buffer, after one cluster barrier.  A pair costs half a warp:
-//   its 16 lanes hold rows g + 16 e, the dot products are 16-lane sums, so
-//   each shuffle serves the two pairs of a warp.
+//   Between outer rounds each block pushes its two blocks into the second
+//   buffers of the blocks that hold them next (bulk copies into distributed
+//   shared memory, completing on the receivers' mbarriers), after one
+//   cluster barrier.  A pair costs half a warp:
+//   its 16 lanes hold the row pairs 32 e + 2 g + {0, 1} (one 8-byte shared
+//   memory access per pair of rows, consecutive across lanes), the dot
+//   products are 16-lane sums, so each shuffle serves the two pairs of a
+//   warp.
 //
 // Accuracy.  The rotation (Rutishauser's formulas, single precision) is
 // orthogonal only to rounding, and in single precision that rounding drifts
@@ -53,12 +56,12 @@
 namespace ffq {
 
 constexpr int JB_G = 16;         // lanes per pair (a warp holds two pairs)
-constexpr int JB_MAX_NE = 14;   // rows per lane (k <= 224 = 16 * 14)
+constexpr int JB_MAX_NE = 7;    // row pairs per lane (k <= 224 = 32 * 7)
 constexpr int JB_MAX_B = 14;    // columns per block (2 C b >= k with C = 8)
 constexpr int JB_MAX_SWEEPS = 40;
 
 struct JbGeom {
-  int C, b, kp, ne, kr, cs, nw;  // blocks of the cluster, block width, padded columns, rows per lane,
+  int C, b, kp, ne, kr, cs, nw;  // blocks of the cluster, block width, padded columns, row pairs per lane,
                                  // padded rows, column stride (floats: X rows then J rows), warps
 };
 
@@ -67,8 +70,8 @@ __host__ __device__ inline JbGeom jb_geom(int k, int C) {
   g.C = C;
   g.b = (k + 2 * C - 1) / (2 * C);
   g.kp = 2 * C * g.b;
-  g.ne = (k + JB_G - 1) / JB_G;
-  g.kr = JB_G * g.ne;
+  g.ne = (k + 2 * JB_G - 1) / (2 * JB_G);
+  g.kr = 2 * JB_G * g.ne;
   g.cs = 2 * g.kr;
   g.nw = (g.b + 1) / 2;  // two pairs per warp: b cross pairs, <= b intra pairs
   return g;
@@ -124,9 +127,11 @@ __device__ __forceinline__ float jb_sum16(float v) {
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) (the smaller angle, |t| <= 1),
 // cs = 1 / sqrt(1 + t^2) refined by one Newton step so that cs^2 + sn^2 = 1
 // to rounding, sn = cs t.
-__device__ __forceinline__ void jb_rotation(float al, float be, float ga, float tol, float &cs, float &sn) {
+__device__ __forceinline__ void jb_rotation(float al, float be, float ga, float tol, float &cs, float &sn,
+                                            float &tn) {
   cs = 1.f;
   sn = 0.f;
+  tn = 0.f;
   if (!(ga != 0.f && ga * ga > (tol * tol) * (al * be))) return;
   const float zeta = __fdividef(be - al, 2.f * ga);
   const float a = fabsf(zeta);
@@ -141,55 +146,114 @@ __device__ __forceinline__ void jb_rotation(float al, float be, float ga, float 
   y = y * fmaf(-0.5f * x, y * y, 1.5f);
   cs = y;
   sn = y * t;
+  tn = t;
 }
 
-// The three dot products of a pair over the lane's rows (packed pairs of
-// rows) summed over the pair's 16 lanes.
-__device__ __forceinline__ void jb_dots(const float *ax, const float *bx, float &al, float &be, float &ga) {
-  float2 a2 = make_float2(0.f, 0.f), b2 = a2, g2 = a2;
+// The three dot products of a pair over the lane's row pairs, summed over
+// the pair's 16 lanes (two accumulators each, to halve the FMA chains).
+__device__ __forceinline__ void jb_dots(const float2 *ax, const float2 *bx, float &al, float &be, float &ga) {
+  float2 a2[2], b2[2], g2[2];
 #pragma unroll
-  for (int e = 0; e < JB_MAX_NE; e += 2) {
-    const float2 xa = make_float2(ax[e], ax[e + 1]), xb = make_float2(bx[e], bx[e + 1]);
-    a2 = __ffma2_rn(xa, xa, a2);
-    b2 = __ffma2_rn(xb, xb, b2);
-    g2 = __ffma2_rn(xa, xb, g2);
+  for (int h = 0; h < 2; ++h) a2[h] = b2[h] = g2[h] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int e = 0; e < JB_MAX_NE; ++e) {
+    a2[e & 1] = __ffma2_rn(ax[e], ax[e], a2[e & 1]);
+    b2[e & 1] = __ffma2_rn(bx[e], bx[e], b2[e & 1]);
+    g2[e & 1] = __ffma2_rn(ax[e], bx[e], g2[e & 1]);
   }
-  al = jb_sum16(a2.x + a2.y);
-  be = jb_sum16(b2.x + b2.y);
-  ga = jb_sum16(g2.x + g2.y);
+  al = jb_sum16((a2[0].x + a2[1].x) + (a2[0].y + a2[1].y));
+  be = jb_sum16((b2[0].x + b2[1].x) + (b2[0].y + b2[1].y));
+  ga = jb_sum16((g2[0].x + g2[1].x) + (g2[0].y + g2[1].y));
 }
 
-// (a, b) <- (cs a - sn b, sn a + cs b) on the lane's rows (packed).
-__device__ __forceinline__ void jb_rotate(float *a, float *b, float cs, float sn) {
+// (a, b) <- (cs a - sn b, sn a + cs b) on the lane's row pairs.
+__device__ __forceinline__ void jb_rotate(float2 *a, float2 *b, float cs, float sn) {
   const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), n2 = make_float2(-sn, -sn);
 #pragma unroll
-  for (int e = 0; e < JB_MAX_NE; e += 2) {
-    const float2 x0 = make_float2(a[e], a[e + 1]), y0 = make_float2(b[e], b[e + 1]);
-    const float2 x1 = __ffma2_rn(c2, x0, __fmul2_rn(n2, y0)), y1 = __ffma2_rn(s2, x0, __fmul2_rn(c2, y0));
-    a[e] = x1.x;
-    a[e + 1] = x1.y;
-    b[e] = y1.x;
-    b[e + 1] = y1.y;
+  for (int e = 0; e < JB_MAX_NE; ++e) {
+    const float2 x0 = a[e], y0 = b[e];
+    a[e] = __ffma2_rn(c2, x0, __fmul2_rn(n2, y0));
+    b[e] = __ffma2_rn(s2, x0, __fmul2_rn(c2, y0));
   }
 }
 
 // Column (X rows then J rows, stride kr between the parts) to registers:
-// lane g of the pair holds rows g + 16 e; rows past the column's ne groups
-// read as zero.
-__device__ __forceinline__ void jb_load(const float *col, int kr, int ne, int g, float *x, float *j) {
+// lane g of the pair holds rows 32 e + 2 g + {0, 1}; row pairs past the
+// column's ne groups read as zero.
+__device__ __forceinline__ void jb_load(const float *col, int kr, int ne, int g, float2 *x, float2 *j) {
 #pragma unroll
   for (int e = 0; e < JB_MAX_NE; ++e) {
-    x[e] = (e < ne) ? col[g + JB_G * e] : 0.f;
-    j[e] = (e < ne) ? col[kr + g + JB_G * e] : 0.f;
+    x[e] = (e < ne) ? *reinterpret_cast<const float2 *>(col + 2 * g + 2 * JB_G * e) : make_float2(0.f, 0.f);
+    j[e] = (e < ne) ? *reinterpret_cast<const float2 *>(col + kr + 2 * g + 2 * JB_G * e) : make_float2(0.f, 0.f);
   }
 }
-__device__ __forceinline__ void jb_store(float *col, int kr, int ne, int g, const float *x, const float *j) {
+__device__ __forceinline__ void jb_store(float *col, int kr, int ne, int g, const float2 *x, const float2 *j) {
 #pragma unroll
   for (int e = 0; e < JB_MAX_NE; ++e)
     if (e < ne) {
-      col[g + JB_G * e] = x[e];
-      col[kr + g + JB_G * e] = j[e];
+      *reinterpret_cast<float2 *>(col + 2 * g + 2 * JB_G * e) = x[e];
+      *reinterpret_cast<float2 *>(col + kr + 2 * g + 2 * JB_G * e) = j[e];
     }
+}
+
+// Block exchange between outer rounds: each block pushes its two column
+// blocks into the blocks that hold them next, with bulk copies from its own
+// shared memory into theirs (the async proxy), each completing on the
+// receiver's mbarrier.  The receiver arms that barrier for the two blocks it
+// will receive before the cluster barrier that ends the round, so the arming
+// precedes every push; every wait is bounded (~1 s) and flags a timeout.
+constexpr long long JB_SPIN = 4000000;
+
+__device__ __forceinline__ uint32_t jb_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t jb_mapa(uint32_t addr, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void jb_mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(jb_smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void jb_mbar_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(jb_smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool jb_mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(jb_smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// A wait gives up after ~1 s of wall time (or JB_SPIN polls), or at once when
+// a timeout was already flagged, so that a failed exchange ends the kernel in
+// seconds with STATUS_TIMEOUT rather than one second per remaining round.
+__device__ __forceinline__ void jb_mbar_wait(uint64_t *bar, uint32_t parity, int *ctl) {
+  if (jb_mbar_try(bar, parity)) return;
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  long long spins = 0;
+  while (!jb_mbar_try(bar, parity)) {
+    if ((++spins & 255) == 0) {
+      unsigned long long t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      if (*((volatile int *)(ctl + CTL_TIMEOUT)) != 0 || t1 - t0 > 1000000000ull || spins > JB_SPIN) {
+        atomicExch(ctl + CTL_TIMEOUT, 1);
+        set_status(ctl, STATUS_TIMEOUT);
+        return;
+      }
+    }
+  }
+}
+// bytes (a multiple of 16) from this block's shared memory at src to the
+// cluster-shared address dst, completing on the cluster-shared mbarrier bar.
+__device__ __forceinline__ void jb_push(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "r"(jb_smem_addr(src)), "r"(bytes), "r"(bar)
+      : "memory");
 }
 
 // M (k x k, row-major, leading dimension ldm) -> Uout = U_s, Vout = V_s
@@ -212,6 +276,7 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
       (reinterpret_cast<uintptr_t>(gid + 2 * b) + 7) & ~(uintptr_t)7);
   double *jnr = xnr + 2 * b;
   __shared__ int s_cnt[2];
+  __shared__ __align__(8) uint64_t s_bar;  // arrival of the next outer round's two blocks
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int q = 2 * w + (lane >> 4);  // pair slot of this half warp
   const int g = lane & (JB_G - 1);    // lane within the pair
@@ -228,8 +293,11 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
     }
   }
   if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) jb_mbar_init(&s_bar);
   __syncthreads();
   cluster.sync();
+  const uint32_t slot_bytes = (uint32_t)(b * cs * sizeof(float));
+  uint32_t bar_phase = 0;
 
   const int ph = b / 2;                     // pairs per block in an intra round
   const int nb = b + (b & 1), m1 = nb - 1;  // players of the intra round-robin (with a bye if b is odd)
@@ -244,7 +312,7 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
     if (ph > 0) {
       for (int t = 0; t < m1; ++t) {
         const bool on = q < 2 * ph;
-        float px[JB_MAX_NE], pj[JB_MAX_NE], qx[JB_MAX_NE], qj[JB_MAX_NE];
+        float2 px[JB_MAX_NE], pj[JB_MAX_NE], qx[JB_MAX_NE], qj[JB_MAX_NE];
         float *cp = B, *cq = B;
         if (on) {
           const int sl = q / ph, i = q % ph + (b & 1);  // odd b: pair 0 holds the bye
@@ -261,9 +329,9 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
         }
         jb_load(cp, kr, on ? ne : 0, g, px, pj);
         jb_load(cq, kr, on ? ne : 0, g, qx, qj);
-        float al, be, ga, c_, s_;
+        float al, be, ga, c_, s_, t_;
         jb_dots(px, qx, al, be, ga);
-        jb_rotation(al, be, ga, tol, c_, s_);
+        jb_rotation(al, be, ga, tol, c_, s_, t_);
         if (on && s_ != 0.f) {
           jb_rotate(px, qx, c_, s_);
           jb_rotate(pj, qj, c_, s_);
@@ -277,17 +345,17 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
     // 2. outer rounds over the blocks
     for (int t = 0; t < n1; ++t) {
       const bool on = q < b;
-      float ax[JB_MAX_NE], aj[JB_MAX_NE];
+      float2 ax[JB_MAX_NE], aj[JB_MAX_NE];
       float *ca = B + (on ? q : 0) * cs;
       jb_load(ca, kr, on ? ne : 0, g, ax, aj);
       int jc = on ? q : 0;  // slot-1 column of inner round r: (q + r) mod b
       for (int r = 0; r < b; ++r) {
         float *cb = B + (b + jc) * cs;
-        float bx[JB_MAX_NE], bj[JB_MAX_NE];
+        float2 bx[JB_MAX_NE], bj[JB_MAX_NE];
         jb_load(cb, kr, on ? ne : 0, g, bx, bj);
-        float al, be, ga, c_, s_;
+        float al, be, ga, c_, s_, t_;
         jb_dots(ax, bx, al, be, ga);
-        jb_rotation(al, be, ga, tol, c_, s_);
+        jb_rotation(al, be, ga, tol, c_, s_, t_);
         if (on && s_ != 0.f) {
           jb_rotate(ax, bx, c_, s_);
           jb_rotate(aj, bj, c_, s_);
@@ -300,7 +368,8 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
       if (on) jb_store(ca, kr, ne, g, ax, aj);
       const bool last = (t == n1 - 1);
       if (last && nrot) atomicAdd(&s_cnt[sweeps & 1], nrot);
-      cluster.sync();  // every block's round-t blocks (and counts) are final
+      if (threadIdx.x == 0) jb_mbar_expect(&s_bar, 2 * slot_bytes);  // this round's two incoming blocks
+      cluster.sync();  // every block's round-t blocks (and counts) are final; every barrier is armed
       if (last) {
         int tot = 0;
         for (int cc = 0; cc < C; ++cc) tot += *cluster.map_shared_rank(&s_cnt[sweeps & 1], (unsigned)cc);
@@ -308,31 +377,21 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
         done = (tot == 0);
         if (done) break;  // the blocks stay where outer round t left them
       }
-      // pull the blocks of the next outer round into the other buffer
+      // push this block's two blocks to the blocks that hold them in the next
+      // outer round (into their other buffer), then wait for the two coming in
       const int tn = last ? 0 : t + 1;
       float *Bn = jb_sm + (cur ^ 1) * bufsz;
-      for (int s = 0; s < 2; ++s) {
-        int oc, os;
-        jb_owner(jb_block_of(c, s, tn, C), t, C, oc, os);
-        const float4 *src = reinterpret_cast<const float4 *>(cluster.map_shared_rank(B, (unsigned)oc) + os * b * cs);
-        float4 *dst = reinterpret_cast<float4 *>(Bn + s * b * cs);
-        const int n4 = b * cs / 4;
-        // four loads in flight per thread before the stores
-        for (int e0 = threadIdx.x; e0 < n4; e0 += 4 * blockDim.x) {
-          float4 v[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n4) v[u] = src[e];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < n4) dst[e] = v[u];
-          }
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int s = 0; s < 2; ++s) {
+          int dc, ds;
+          jb_owner(jb_block_of(c, s, t, C), tn, C, dc, ds);
+          jb_push(jb_mapa(jb_smem_addr(Bn + ds * b * cs), (unsigned)dc), B + s * b * cs, slot_bytes,
+                  jb_mapa(jb_smem_addr(&s_bar), (unsigned)dc));
         }
       }
-      __syncthreads();
+      jb_mbar_wait(&s_bar, bar_phase, ctl);
+      bar_phase ^= 1;
       cur ^= 1;
       B = Bn;
       tpos = tn;
