@@ -300,15 +300,32 @@ int ffsrqr_batch_run(ffsrqr_batch_t batch, const ffsrqr_problem_t *probs, void *
                      ffsrqr_info_t *infos);
 
 /* Autotuner: times the batch graph (3 launches after a warm-up) with 1, 2,
- * 4 and 8 streams on stream and keeps the fastest; writes it to *chosen and
- * its milliseconds per launch to *ms_best (either may be NULL).  The batch's
- * outputs hold the results of the last timed launch.  Returns as
- * ffsrqr_batch_run. */
+ * 4 and 8 streams, plain and phase-batched, on stream and keeps the fastest;
+ * writes its stream count to *chosen and its milliseconds per launch to
+ * *ms_best (either may be NULL; ffsrqr_batch_phased reports the other
+ * choice).  The batch's outputs hold the results of the last timed launch.
+ * Returns as ffsrqr_batch_run. */
 int ffsrqr_batch_tune(ffsrqr_batch_t batch, const ffsrqr_problem_t *probs, void *workspace, void *stream,
                       ffsrqr_info_t *infos, int32_t *chosen, float *ms_best);
 
 /* Current stream count of the batch (-1 for NULL). */
 int ffsrqr_batch_streams(ffsrqr_batch_t batch);
+
+/* Phase-batched graph (phased = 1): the streams run every problem up to its
+ * small SVD (Alg. 9, "svd(tmp)"), join, one launch per cluster size takes the
+ * small SVDs of all single-precision problems whose SRQR depth is k together
+ * (the column-block Jacobi of each problem on its own thread-block cluster),
+ * then the streams fork again for the rest.  Results are bitwise those of the
+ * plain graph (phased = 0, the default).  The next ffsrqr_batch_run
+ * re-captures.  Returns 0, -1 NULL batch, -2 phased not 0 or 1. */
+int ffsrqr_batch_set_phased(ffsrqr_batch_t batch, int32_t phased);
+
+/* 1 if the batch builds phase-batched graphs, 0 if not, -1 for NULL. */
+int ffsrqr_batch_phased(ffsrqr_batch_t batch);
+
+/* Batched small-SVD launches in the captured graph (0 or more), -1 for NULL,
+ * before the first capture, or when the graph is not phase-batched. */
+int ffsrqr_batch_small_svd_launches(ffsrqr_batch_t batch);
 
 /* Byte offset of problem i's workspace slice and its plan (for
  * ffsrqr_workspace_item).  Returns 0, -1 NULL batch, -2 i out of range. */
@@ -420,6 +437,25 @@ int ffsrqr_server_wait(ffsrqr_server_t server, int64_t ticket, ffsrqr_info_t *in
  * (any pointer may be NULL). */
 int ffsrqr_server_stats(ffsrqr_server_t server, int64_t *admitted, int64_t *completed, int64_t *queued,
                         size_t *arena_free);
+
+/* Same-phase batching (on = 1; 0, the default, turns it off): the requests
+ * admitted in one pass of the scheduler whose small SVD (Alg. 9,
+ * "svd(tmp)") is the single-precision column-block Jacobi (FP32 and mixed
+ * modes, SRQR depth k) run up to the small SVD on their slot streams; one
+ * launch per thread-block-cluster size then takes all their small SVDs, and
+ * each request finishes on its own stream.  Results are bitwise those of the
+ * request run alone.  Returns 0, -1 NULL server, -2 on not 0 or 1. */
+int ffsrqr_server_set_phase_batch(ffsrqr_server_t server, int32_t on);
+
+/* paused = 1 holds admission (requests queue; running ones go on), 0 resumes
+ * it, so that requests submitted while paused are admitted in one pass (and,
+ * with same-phase batching, share their small-SVD launches).  Returns 0, -1
+ * NULL server, -2 paused not 0 or 1. */
+int ffsrqr_server_pause(ffsrqr_server_t server, int32_t paused);
+
+/* Same-phase batching counters: batched small-SVD launches so far and the
+ * requests they covered (either pointer may be NULL). */
+int ffsrqr_server_phase_stats(ffsrqr_server_t server, int64_t *small_svd_launches, int64_t *grouped_requests);
 
 /* Stops the scheduler (running requests finish first) and frees the arena. */
 int ffsrqr_server_destroy(ffsrqr_server_t server);

@@ -11,8 +11,12 @@
 // The graph is instantiated once and launched on the caller's stream, one
 // cudaGraphLaunch per run, so a batch of hundreds of small problems costs one host launch and the
 // device overlaps the small problems' latency-bound phases across streams.
-// ffsrqr_batch_tune times the graph for S in {1, 2, 4, 8} and keeps the
-// fastest.
+// Phase-batched graphs (ffsrqr_batch_set_phased): the streams run every
+// problem up to its small SVD, join, one launch per cluster size takes the
+// small SVDs of all single-precision problems together, and the streams fork
+// again for the rest of each pipeline (results bitwise those of the plain
+// graph).  ffsrqr_batch_tune times the graph for S in {1, 2, 4, 8}, plain and
+// phase-batched, and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +28,14 @@
 #include "../../include/ffsrqr.h"
 
 void ffq_set_last_error(const char *what, cudaError_t e);  // ffsrqr.cu
+// phase-batched runs (ffsrqr.cu)
+bool ffq_phase_batchable(ffsrqr_plan_t P);
+int ffq_run_pre(ffsrqr_plan_t P, const void *A, int64_t lda, uint64_t seed, int32_t *piv, void *workspace,
+                cudaStream_t st);
+int ffq_run_post(ffsrqr_plan_t P, const void *A, int64_t lda, void *U, int64_t ldu, void *V, int64_t ldv,
+                 int32_t *piv, void *workspace, cudaStream_t st, ffsrqr_info_t *info);
+int ffq_small_svd_batched(const ffsrqr_plan_t *plans, void *const *workspaces, void *const *S, int count,
+                          cudaStream_t st, int *launches);
 
 namespace {
 
@@ -48,13 +60,16 @@ struct ffsrqr_batch_s {
   int streams = 4;
   std::vector<cudaStream_t> st;
   cudaStream_t cap = nullptr;  // capture origin (the caller's stream may be the legacy stream)
-  cudaEvent_t fork = nullptr;
+  cudaEvent_t fork = nullptr, fork2 = nullptr;
   std::vector<cudaEvent_t> join;
+  int phased = 0;           // phase-batched graph
+  int svd_launches = -1;    // batched small-SVD launches in the captured graph (-1: none)
   cudaGraphExec_t exec = nullptr;
   std::vector<ffsrqr_problem_t> key;  // problems the graph was captured with
   void *key_ws = nullptr;
   ffsrqr_info_t *key_info = nullptr;
   int key_streams = 0;
+  int key_phased = 0;
 };
 
 namespace {
@@ -66,7 +81,9 @@ void drop_graph(ffsrqr_batch_s *b) {
 }
 
 bool same_problems(const ffsrqr_batch_s *b, const ffsrqr_problem_t *probs, void *ws, ffsrqr_info_t *infos) {
-  if (!b->exec || b->key_ws != ws || b->key_info != infos || b->key_streams != b->streams) return false;
+  if (!b->exec || b->key_ws != ws || b->key_info != infos || b->key_streams != b->streams ||
+      b->key_phased != b->phased)
+    return false;
   return std::memcmp(b->key.data(), probs, sizeof(ffsrqr_problem_t) * b->count) == 0;
 }
 
@@ -100,18 +117,51 @@ int capture(ffsrqr_batch_s *b, const ffsrqr_problem_t *probs, void *workspace, f
   if ((ce = cudaEventRecord(b->fork, stream)) != cudaSuccess) err = cuda_fail("cudaEventRecord(fork)", ce);
   for (int s = 0; s < S && !err; ++s)
     if ((ce = cudaStreamWaitEvent(b->st[s], b->fork, 0)) != cudaSuccess) err = cuda_fail("cudaStreamWaitEvent", ce);
+  auto join_all = [&]() {
+    for (int s = 0; s < S && !err; ++s) {
+      if ((ce = cudaEventRecord(b->join[s], b->st[s])) != cudaSuccess ||
+          (ce = cudaStreamWaitEvent(stream, b->join[s], 0)) != cudaSuccess)
+        err = cuda_fail("join", ce);
+    }
+  };
+  std::vector<ffsrqr_plan_t> bp;  // phase-batched problems, in stream order
+  std::vector<void *> bws, bS;
+  std::vector<int> bidx;
   for (int j = 0; j < b->count && !err; ++j) {
     const int i = b->order[j];
     const ffsrqr_problem_t &q = probs[i];
     unsigned char *ws = reinterpret_cast<unsigned char *>(workspace) + b->off[i];
-    const int r = ffsrqr_run(b->plans[i], q.A, q.lda, q.seed, q.U, q.ldu, q.S, q.V, q.ldv, q.piv, ws,
-                             b->st[j % S], infos ? infos + i : nullptr);
+    int r;
+    if (b->phased && ffq_phase_batchable(b->plans[i])) {
+      r = ffq_run_pre(b->plans[i], q.A, q.lda, q.seed, q.piv, ws, b->st[j % S]);
+      bp.push_back(b->plans[i]);
+      bws.push_back(ws);
+      bS.push_back(q.S);
+      bidx.push_back(j);
+    } else {
+      r = ffsrqr_run(b->plans[i], q.A, q.lda, q.seed, q.U, q.ldu, q.S, q.V, q.ldv, q.piv, ws, b->st[j % S],
+                     infos ? infos + i : nullptr);
+    }
     if (r) err = r;
   }
-  for (int s = 0; s < S && !err; ++s) {
-    if ((ce = cudaEventRecord(b->join[s], b->st[s])) != cudaSuccess ||
-        (ce = cudaStreamWaitEvent(stream, b->join[s], 0)) != cudaSuccess)
-      err = cuda_fail("join", ce);
+  join_all();
+  b->svd_launches = -1;
+  if (!err && !bp.empty()) {
+    int nl = 0;
+    const int r = ffq_small_svd_batched(bp.data(), bws.data(), bS.data(), (int)bp.size(), stream, &nl);
+    if (r) err = r;
+    b->svd_launches = nl;
+    if (!err && (ce = cudaEventRecord(b->fork2, stream)) != cudaSuccess) err = cuda_fail("cudaEventRecord(fork2)", ce);
+    for (int s = 0; s < S && !err; ++s)
+      if ((ce = cudaStreamWaitEvent(b->st[s], b->fork2, 0)) != cudaSuccess) err = cuda_fail("cudaStreamWaitEvent", ce);
+    for (size_t e = 0; e < bidx.size() && !err; ++e) {
+      const int j = bidx[e], i = b->order[j];
+      const ffsrqr_problem_t &q = probs[i];
+      const int r2 = ffq_run_post(b->plans[i], q.A, q.lda, q.U, q.ldu, q.V, q.ldv, q.piv, bws[e], b->st[j % S],
+                                  infos ? infos + i : nullptr);
+      if (r2) err = r2;
+    }
+    join_all();
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(stream, &graph);
@@ -129,6 +179,7 @@ int capture(ffsrqr_batch_s *b, const ffsrqr_problem_t *probs, void *workspace, f
   b->key_ws = workspace;
   b->key_info = infos;
   b->key_streams = S;
+  b->key_phased = b->phased;
   return 0;
 }
 
@@ -170,6 +221,7 @@ int ffsrqr_batch_create(ffsrqr_batch_t *batch, int32_t count, const int64_t *m, 
                    [&](int x, int y) { return (double)m[x] * n[x] > (double)m[y] * n[y]; });
   cudaError_t ce;
   if ((ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     ffsrqr_batch_destroy(b);
     return cuda_fail("batch set-up", ce);
@@ -205,12 +257,13 @@ int ffsrqr_batch_tune(ffsrqr_batch_t b, const ffsrqr_problem_t *probs, void *wor
     cudaEventDestroy(e0);
     return FFSRQR_STATUS_CUDA;
   }
-  int best = b->streams;
+  int best = b->streams, best_phased = b->phased;
   float best_ms = -1.f;
   int rc = 0;
   const int cand[4] = {1, 2, 4, 8};
-  for (int c = 0; c < 4 && !rc; ++c) {
-    b->streams = cand[c];
+  for (int c = 0; c < 8 && !rc; ++c) {
+    b->streams = cand[c % 4];
+    b->phased = c / 4;
     if ((rc = ffsrqr_batch_run(b, probs, workspace, stream, infos))) break;  // capture + warm-up
     if (cudaEventRecord(e0, st) != cudaSuccess) {
       rc = FFSRQR_STATUS_CUDA;
@@ -227,12 +280,14 @@ int ffsrqr_batch_tune(ffsrqr_batch_t b, const ffsrqr_problem_t *probs, void *wor
     t /= 3.f;
     if (best_ms < 0.f || t < best_ms) {
       best_ms = t;
-      best = cand[c];
+      best = cand[c % 4];
+      best_phased = c / 4;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->streams = best;
+  b->phased = best_phased;
   drop_graph(b);
   if (rc) return rc;
   if (chosen) *chosen = best;
@@ -241,6 +296,17 @@ int ffsrqr_batch_tune(ffsrqr_batch_t b, const ffsrqr_problem_t *probs, void *wor
 }
 
 int ffsrqr_batch_streams(ffsrqr_batch_t b) { return b ? b->streams : -1; }
+
+int ffsrqr_batch_set_phased(ffsrqr_batch_t b, int32_t phased) {
+  if (!b) return -1;
+  if (phased != 0 && phased != 1) return -2;
+  b->phased = phased;
+  return 0;
+}
+
+int ffsrqr_batch_phased(ffsrqr_batch_t b) { return b ? b->phased : -1; }
+
+int ffsrqr_batch_small_svd_launches(ffsrqr_batch_t b) { return (b && b->exec) ? b->svd_launches : -1; }
 
 int ffsrqr_batch_workspace_offset(ffsrqr_batch_t b, int32_t i, size_t *offset, ffsrqr_plan_t *plan) {
   if (!b) return -1;
@@ -258,6 +324,7 @@ int ffsrqr_batch_destroy(ffsrqr_batch_t b) {
     cudaEventDestroy(b->join[s]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->fork2) cudaEventDestroy(b->fork2);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (ffsrqr_plan_t pl : b->plans)
     if (pl) ffsrqr_destroy(pl);

@@ -22,11 +22,13 @@
 // basis of the same column space as Householder QR.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/ffsrqr.h"
 #include "common.cuh"
@@ -686,14 +688,19 @@ cudaError_t launch_jacobi_blk(cudaStream_t st, const float *M, int kk, int ldm, 
   return cudaLaunchKernelEx(&cfg, jacobi_blk_kernel, M, kk, ldm, tol, (int)JB_MAX_SWEEPS, Us, S, Vs, ctl);
 }
 
+// Alg. 9 up to the small SVD: a1-a10 without the SVD of M_t (M_t, workspace
+// item 8, and Q_t, V' in place).  The phase-batched runs of a batch or a
+// server run this part of several problems, their small SVDs in one launch,
+// then run_post.
 template <typename T>
-int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
-             int64_t ldv, int32_t *piv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
+int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *piv, unsigned char *ws,
+            cudaStream_t st) {
   const int64_t m = P->m, n = P->n;
   const int k = P->k, s = P->s;
   const int64_t ldm = P->ldm, lds = P->lds, ldk = P->ldk;
   WsPtrs<T> w = ws_ptrs<T>(P, ws);
   const int nsm = P->num_sms;
+  const bool tc = use_tc<T>(P, A, lda);
   int rc;
 
   CK(cudaMemsetAsync(ws + P->off_ctl, 0, CTL_WORDS * sizeof(int), st));
@@ -715,7 +722,6 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
                                                                                          seed);
     CKL("omega");
   }
-  const bool tc = use_tc<T>(P, A, lda);
   MARK(1);
   // a2: pass 1, B^T (n x s) = A^T Omega^T
   if (tc && P->mode == FFSRQR_MIXED_BF16X3) {
@@ -887,6 +893,15 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.rt, k, false, w.r11, k, true, w.t1, k))) return rc;
   if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.t1, k, false, w.rz, k, false, w.mt, k))) return rc;
   MARK(10);
+  return 0;
+}
+
+// The SVD of M_t (k x k): S (k) and U_s, V_s into the workspace.
+template <typename T>
+int run_small_svd(ffsrqr_plan_s *P, T *S, unsigned char *ws, cudaStream_t st) {
+  const int k = P->k;
+  WsPtrs<T> w = ws_ptrs<T>(P, ws);
+  int rc;
   if constexpr (sizeof(T) == 4) {
     // single precision: column-block cluster Jacobi on M_t^T
     CK(launch_jacobi_blk(st, (const float *)w.mt, k, k, (float *)w.us, (float *)S, (float *)w.vs, w.ctl));
@@ -909,6 +924,21 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
     CK(cudaStreamWaitEvent(st, P->ev_join, 0));
     if ((rc = launch_gemm<T>(st, P, ws, k, k, k, w.qg, k, true, w.t1, k, true, w.vs, k))) return rc;
   }
+  return 0;
+}
+
+// Alg. 9 after the small SVD: a11 (U = Q_t U_s, V = V' V_s, the sign rule),
+// the pivot tail and the report.
+template <typename T>
+int run_post(ffsrqr_plan_s *P, const T *A, int64_t lda, T *U, int64_t ldu, T *V, int64_t ldv, int32_t *piv,
+             unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
+  const int64_t m = P->m, n = P->n;
+  const int k = P->k;
+  const int64_t ldk = P->ldk;
+  WsPtrs<T> w = ws_ptrs<T>(P, ws);
+  const int nsm = P->num_sms;
+  const bool tc = use_tc<T>(P, A, lda);
+  int rc;
   MARK(11);
   // a11: U = Q_t U_s, V = V' V_s, sign rule
   if (tc) {
@@ -938,6 +968,15 @@ int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int
   CKL("info");
   if (info) CK(cudaMemcpyAsync(info, dinfo, sizeof(ffsrqr_info_t), cudaMemcpyDeviceToHost, st));
   return 0;
+}
+
+template <typename T>
+int run_impl(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, T *U, int64_t ldu, T *S, T *V,
+             int64_t ldv, int32_t *piv, unsigned char *ws, cudaStream_t st, ffsrqr_info_t *info) {
+  int rc;
+  if ((rc = run_pre<T>(P, A, lda, seed, piv, ws, st))) return rc;
+  if ((rc = run_small_svd<T>(P, S, ws, st))) return rc;
+  return run_post<T>(P, A, lda, U, ldu, V, ldv, piv, ws, st, info);
 }
 
 // Alg. 9 with SRQR depth l = P->k above the target rank kout: the depth-l
@@ -1480,6 +1519,92 @@ int ffq_gemm_nt(ffsrqr_plan_t P, int64_t m, int64_t n, int r, const void *U, int
                             false, (float *)X, ldx);
   *launches = g_launches;
   return rc;
+}
+
+// Phase-batched runs.  A batch graph or a server group runs part 1 (everything
+// before the small SVD) of several problems, one launch of their small SVDs,
+// then part 2.  Only plans whose small SVD is the single-precision cluster
+// Jacobi take part (FP32 arithmetic, SRQR depth l = k, not the subspace
+// iteration); every result is bitwise the one ffsrqr_run gives.
+bool ffq_phase_batchable(ffsrqr_plan_t P) { return P && P->elem == 4 && P->rsi_q < 0 && P->kout == P->k; }
+
+int ffq_run_pre(ffsrqr_plan_t P, const void *A, int64_t lda, uint64_t seed, int32_t *piv, void *workspace,
+                cudaStream_t st) {
+  if (!ffq_phase_batchable(P)) return -1;
+  if (!A || lda < P->n || !piv || !workspace || ((uintptr_t)workspace & 255u)) return -2;
+  P->evset = (int)(P->runs & 1);
+  ++P->runs;
+  return run_pre<float>(P, (const float *)A, lda, seed, piv, reinterpret_cast<unsigned char *>(workspace), st);
+}
+
+int ffq_run_post(ffsrqr_plan_t P, const void *A, int64_t lda, void *U, int64_t ldu, void *V, int64_t ldv,
+                 int32_t *piv, void *workspace, cudaStream_t st, ffsrqr_info_t *info) {
+  if (!ffq_phase_batchable(P)) return -1;
+  if (!A || !U || ldu < P->k || !V || ldv < P->k || !piv || !workspace) return -2;
+  return run_post<float>(P, (const float *)A, lda, (float *)U, ldu, (float *)V, ldv, piv,
+                         reinterpret_cast<unsigned char *>(workspace), st, info);
+}
+
+// The small SVDs of count phase-batchable problems (after their part 1, in
+// stream order): one jacobi_blk_batch_kernel launch per cluster size and
+// JB_BATCH_MAX problems.  S[i] is problem i's singular-value output.  Writes
+// the number of launches to *launches.
+int ffq_small_svd_batched(const ffsrqr_plan_t *plans, void *const *workspaces, void *const *S, int count,
+                          cudaStream_t st, int *launches) {
+  int nl = 0;
+  std::vector<char> done(count, 0);
+  for (int i0 = 0; i0 < count; ++i0) {
+    if (done[i0]) continue;
+    const int C = jb_cluster_for(plans[i0]->k);
+    std::vector<int> grp;
+    for (int i = i0; i < count; ++i)
+      if (!done[i] && jb_cluster_for(plans[i]->k) == C) {
+        grp.push_back(i);
+        done[i] = 1;
+      }
+    for (size_t g0 = 0; g0 < grp.size(); g0 += JB_BATCH_MAX) {
+      const int ng = (int)std::min<size_t>(JB_BATCH_MAX, grp.size() - g0);
+      JbBatch jb{};
+      jb.count = ng;
+      jb.max_sweeps = JB_MAX_SWEEPS;
+      int nw = 1;
+      size_t smem = 0;
+      for (int e = 0; e < ng; ++e) {
+        ffsrqr_plan_s *P = plans[grp[g0 + e]];
+        if (!ffq_phase_batchable(P)) return -1;
+        const int k = P->k;
+        WsPtrs<float> w = ws_ptrs<float>(P, reinterpret_cast<unsigned char *>(workspaces[grp[g0 + e]]));
+        JbProblem &q = jb.p[e];
+        q.M = w.mt;
+        q.U = w.us;
+        q.S = reinterpret_cast<float *>(S[grp[g0 + e]]);
+        q.V = w.vs;
+        q.ctl = w.ctl;
+        q.k = k;
+        q.ldm = k;
+        q.tol = 4.f * sqrtf((float)k) * 5.9604645e-8f;  // as launch_jacobi_blk
+        nw = std::max(nw, jb_geom(k, C).nw);
+        smem = std::max(smem, jb_smem_bytes(k));
+      }
+      CK(smem_cap_max((const void *)jacobi_blk_batch_kernel));
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(ng * C));
+      cfg.blockDim = dim3((unsigned)(32 * nw));
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      CK(cudaLaunchKernelEx(&cfg, jacobi_blk_batch_kernel, jb));
+      ++nl;
+    }
+  }
+  if (launches) *launches = nl;
+  return 0;
 }
 
 extern "C" {

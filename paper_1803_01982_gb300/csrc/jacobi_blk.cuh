@@ -259,9 +259,9 @@ __device__ __forceinline__ void jb_push(uint32_t dst, const void *src, uint32_t 
 // M (k x k, row-major, leading dimension ldm) -> Uout = U_s, Vout = V_s
 // (k x k, row-major, leading dimension k), Sout (k, descending).  Cluster of
 // C = jb_cluster_for(k) blocks of 32 * jb_geom(k, C).nw threads.
-__global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
-    const float *__restrict__ M, int k, int ldm, float tol, int max_sweeps, float *__restrict__ Uout,
-    float *__restrict__ Sout, float *__restrict__ Vout, int *ctl) {
+__device__ __forceinline__ void jacobi_blk_body(const float *__restrict__ M, int k, int ldm, float tol,
+                                                int max_sweeps, float *__restrict__ Uout,
+                                                float *__restrict__ Sout, float *__restrict__ Vout, int *ctl) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -449,6 +449,37 @@ __global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
     if (lane == 0) Sout[rk] = sc;
   }
   cluster.sync();  // no block leaves while another may still read its sigma and ids
+}
+
+__global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_kernel(
+    const float *__restrict__ M, int k, int ldm, float tol, int max_sweeps, float *__restrict__ Uout,
+    float *__restrict__ Sout, float *__restrict__ Vout, int *ctl) {
+  jacobi_blk_body(M, k, ldm, tol, max_sweeps, Uout, Sout, Vout, ctl);
+}
+
+// Several problems' small SVDs in one launch: cluster i (blocks
+// i C .. i C + C - 1) runs problem i exactly as jacobi_blk_kernel would (the
+// same cluster size C for all of them, blockDim the largest any of them
+// needs: warps past a problem's own need take no pair), so every result is
+// bitwise the one a launch of its own gives.
+struct JbProblem {
+  const float *M;
+  float *U, *S, *V;
+  int *ctl;
+  int k, ldm;
+  float tol;
+};
+constexpr int JB_BATCH_MAX = 32;  // problems per launch (the descriptors travel as kernel parameters)
+struct JbBatch {
+  int count, max_sweeps;
+  JbProblem p[JB_BATCH_MAX];
+};
+
+__global__ void __launch_bounds__(32 * ((JB_MAX_B + 1) / 2)) jacobi_blk_batch_kernel(const JbBatch batch) {
+  namespace cg = cooperative_groups;
+  const int i = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+  const JbProblem &q = batch.p[i];
+  jacobi_blk_body(q.M, q.k, q.ldm, q.tol, batch.max_sweeps, q.U, q.S, q.V, q.ctl);
 }
 
 }  // namespace ffq

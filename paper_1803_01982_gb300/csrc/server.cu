@@ -15,6 +15,15 @@
 // Plans are cached by (m, n, k, p, mode).  A request whose workspace exceeds
 // the whole budget is refused at submission (FFSRQR_STATUS_WORKSPACE).
 // Latency = completion seen by the scheduler - submission (host steady clock).
+//
+// Same-phase batching (ffsrqr_server_set_phase_batch): the requests admitted
+// in one pass of the scheduler whose small SVD can be batched (single
+// precision, SRQR depth k) run their pipelines up to the small SVD on their
+// slot streams, a group stream waits for all of them and takes their small
+// SVDs in one launch per cluster size, and each slot stream waits for that
+// before the rest of its pipeline.  Results are bitwise those of a request
+// run alone.  ffsrqr_server_pause holds admission, so that requests
+// submitted meanwhile are admitted (and batched) together.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -30,6 +39,15 @@
 #include <vector>
 
 #include "../../include/ffsrqr.h"
+
+// phase-batched runs (ffsrqr.cu)
+bool ffq_phase_batchable(ffsrqr_plan_t P);
+int ffq_run_pre(ffsrqr_plan_t P, const void *A, int64_t lda, uint64_t seed, int32_t *piv, void *workspace,
+                cudaStream_t st);
+int ffq_run_post(ffsrqr_plan_t P, const void *A, int64_t lda, void *U, int64_t ldu, void *V, int64_t ldv,
+                 int32_t *piv, void *workspace, cudaStream_t st, ffsrqr_info_t *info);
+int ffq_small_svd_batched(const ffsrqr_plan_t *plans, void *const *workspaces, void *const *S, int count,
+                          cudaStream_t st, int *launches);
 
 namespace {
 
@@ -95,6 +113,11 @@ struct ffsrqr_server_s {
   int slots = 0;
   std::vector<cudaStream_t> st;
   std::vector<cudaEvent_t> done_ev;
+  std::vector<cudaEvent_t> pre_ev;  // per slot: its request's part before the small SVD
+  cudaStream_t grp = nullptr;       // batched small SVDs
+  cudaEvent_t grp_ev = nullptr;
+  bool phase_batch = false, paused = false;
+  int64_t grp_launches = 0, grp_requests = 0;
   std::vector<int64_t> slot_req;  // ticket running in the slot, -1 if free
   ffsrqr_info_t *slot_info = nullptr;  // pinned, one per slot
   ffsrqr_opts_t opts{};
@@ -128,6 +151,84 @@ int plan_for(ffsrqr_server_s *s, const ffsrqr_request_t &r, ffsrqr_plan_t *plan,
   return 0;
 }
 
+// A request that failed to start: let its stream drain before its
+// workspace can be reused.  Caller holds s->mu.
+void fail_start(ffsrqr_server_s *s, int64_t t, int rc) {
+  Req &rq = s->reqs[t];
+  rq.state = 3;
+  rq.rc = rc ? rc : FFSRQR_STATUS_CUDA;
+  rq.t_done = now_s();
+  cudaStreamSynchronize(s->st[rq.slot]);
+  s->arena.release(rq.off, rq.need);
+  s->slot_req[rq.slot] = -1;
+  ++s->completed;
+}
+
+// Start the admitted requests (slots and workspaces reserved).  Caller holds
+// s->mu.
+void start(ffsrqr_server_s *s, const std::vector<int64_t> &adm) {
+  std::vector<int64_t> grp;
+  for (int64_t t : adm) {
+    Req &rq = s->reqs[t];
+    if (s->phase_batch && ffq_phase_batchable(rq.plan)) {
+      grp.push_back(t);
+      continue;
+    }
+    const ffsrqr_request_t &r = rq.r;
+    const int slot = rq.slot;
+    const int rc = ffsrqr_run(rq.plan, r.A, r.lda, r.seed, r.U, r.ldu, r.S, r.V, r.ldv, r.piv,
+                              s->arena_base + rq.off, s->st[slot], s->slot_info + slot);
+    if (rc || cudaEventRecord(s->done_ev[slot], s->st[slot]) != cudaSuccess) {
+      fail_start(s, t, rc);
+    } else {
+      rq.state = 1;
+      ++s->admitted;
+    }
+  }
+  if (grp.empty()) return;
+  // same-phase batch: parts before the small SVD, one batched small SVD per
+  // cluster size on the group stream, then the rest
+  int rc = 0;
+  std::vector<ffsrqr_plan_t> plans;
+  std::vector<void *> wss, Ss;
+  for (int64_t t : grp) {
+    Req &rq = s->reqs[t];
+    const ffsrqr_request_t &r = rq.r;
+    void *ws = s->arena_base + rq.off;
+    if (!rc) rc = ffq_run_pre(rq.plan, r.A, r.lda, r.seed, r.piv, ws, s->st[rq.slot]);
+    if (!rc && cudaEventRecord(s->pre_ev[rq.slot], s->st[rq.slot]) != cudaSuccess) rc = FFSRQR_STATUS_CUDA;
+    if (!rc && cudaStreamWaitEvent(s->grp, s->pre_ev[rq.slot], 0) != cudaSuccess) rc = FFSRQR_STATUS_CUDA;
+    plans.push_back(rq.plan);
+    wss.push_back(ws);
+    Ss.push_back(r.S);
+  }
+  int nl = 0;
+  if (!rc) rc = ffq_small_svd_batched(plans.data(), wss.data(), Ss.data(), (int)plans.size(), s->grp, &nl);
+  if (!rc && cudaEventRecord(s->grp_ev, s->grp) != cudaSuccess) rc = FFSRQR_STATUS_CUDA;
+  for (size_t e = 0; e < grp.size(); ++e) {
+    Req &rq = s->reqs[grp[e]];
+    const ffsrqr_request_t &r = rq.r;
+    const int slot = rq.slot;
+    int rr = rc;
+    if (!rr && cudaStreamWaitEvent(s->st[slot], s->grp_ev, 0) != cudaSuccess) rr = FFSRQR_STATUS_CUDA;
+    if (!rr)
+      rr = ffq_run_post(rq.plan, r.A, r.lda, r.U, r.ldu, r.V, r.ldv, r.piv, wss[e], s->st[slot],
+                        s->slot_info + slot);
+    if (!rr && cudaEventRecord(s->done_ev[slot], s->st[slot]) != cudaSuccess) rr = FFSRQR_STATUS_CUDA;
+    if (rr) {
+      if (!rc) cudaStreamSynchronize(s->grp);
+      fail_start(s, grp[e], rr);
+    } else {
+      rq.state = 1;
+      ++s->admitted;
+    }
+  }
+  if (!rc) {
+    s->grp_launches += nl;
+    s->grp_requests += (int64_t)grp.size();
+  }
+}
+
 void scheduler(ffsrqr_server_s *s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lock(s->mu);
@@ -149,8 +250,10 @@ void scheduler(ffsrqr_server_s *s) {
       ++s->completed;
       progress = true;
     }
-    // admit queued requests in arrival order
-    while (!s->queue.empty()) {
+    // admit queued requests in arrival order: first take slots and memory,
+    // then start them (together, when same-phase batching is on)
+    std::vector<int64_t> adm;
+    while (!s->paused && !s->queue.empty()) {
       int slot = -1;
       for (int k = 0; k < s->slots; ++k)
         if (s->slot_req[k] < 0) {
@@ -165,22 +268,11 @@ void scheduler(ffsrqr_server_s *s) {
       s->queue.pop_front();
       rq.off = off;
       rq.slot = slot;
-      const ffsrqr_request_t &r = rq.r;
-      const int rc = ffsrqr_run(rq.plan, r.A, r.lda, r.seed, r.U, r.ldu, r.S, r.V, r.ldv, r.piv,
-                                s->arena_base + off, s->st[slot], s->slot_info + slot);
-      if (rc || cudaEventRecord(s->done_ev[slot], s->st[slot]) != cudaSuccess) {
-        rq.state = 3;
-        rq.rc = rc ? rc : FFSRQR_STATUS_CUDA;
-        rq.t_done = now_s();
-        // let the stream drain before the workspace can be reused
-        cudaStreamSynchronize(s->st[slot]);
-        s->arena.release(off, rq.need);
-        ++s->completed;
-      } else {
-        rq.state = 1;
-        s->slot_req[slot] = t;
-        ++s->admitted;
-      }
+      s->slot_req[slot] = t;  // reserved; reset below if the start fails
+      adm.push_back(t);
+    }
+    if (!adm.empty()) {
+      start(s, adm);
       progress = true;
     }
     if (progress) s->cv.notify_all();
@@ -213,12 +305,16 @@ int ffsrqr_server_create(ffsrqr_server_t *server, size_t budget_bytes, int32_t s
   s->slots = slots;
   s->st.assign(slots, nullptr);
   s->done_ev.assign(slots, nullptr);
+  s->pre_ev.assign(slots, nullptr);
   s->slot_req.assign(slots, -1);
   bool ok = cudaHostAlloc(&s->slot_info, sizeof(ffsrqr_info_t) * slots, cudaHostAllocDefault) == cudaSuccess;
   for (int k = 0; k < slots && ok; ++k) {
     ok = cudaStreamCreateWithFlags(&s->st[k], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&s->done_ev[k], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&s->done_ev[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->pre_ev[k], cudaEventDisableTiming) == cudaSuccess;
   }
+  ok = ok && cudaStreamCreateWithFlags(&s->grp, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&s->grp_ev, cudaEventDisableTiming) == cudaSuccess;
   if (opts) {
     s->opts = *opts;
     s->has_opts = true;
@@ -295,6 +391,33 @@ int ffsrqr_server_stats(ffsrqr_server_t s, int64_t *admitted, int64_t *completed
   return 0;
 }
 
+int ffsrqr_server_set_phase_batch(ffsrqr_server_t s, int32_t on) {
+  if (!s) return -1;
+  if (on != 0 && on != 1) return -2;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->phase_batch = (on == 1);
+  return 0;
+}
+
+int ffsrqr_server_pause(ffsrqr_server_t s, int32_t paused) {
+  if (!s) return -1;
+  if (paused != 0 && paused != 1) return -2;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->paused = (paused == 1);
+  }
+  s->cv.notify_all();
+  return 0;
+}
+
+int ffsrqr_server_phase_stats(ffsrqr_server_t s, int64_t *small_svd_launches, int64_t *grouped_requests) {
+  if (!s) return -1;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (small_svd_launches) *small_svd_launches = s->grp_launches;
+  if (grouped_requests) *grouped_requests = s->grp_requests;
+  return 0;
+}
+
 int ffsrqr_server_destroy(ffsrqr_server_t s) {
   if (!s) return -1;
   {
@@ -309,7 +432,13 @@ int ffsrqr_server_destroy(ffsrqr_server_t s) {
       cudaStreamDestroy(s->st[k]);
     }
     if (s->done_ev[k]) cudaEventDestroy(s->done_ev[k]);
+    if (s->pre_ev[k]) cudaEventDestroy(s->pre_ev[k]);
   }
+  if (s->grp) {
+    cudaStreamSynchronize(s->grp);
+    cudaStreamDestroy(s->grp);
+  }
+  if (s->grp_ev) cudaEventDestroy(s->grp_ev);
   for (auto &kv : s->plans) ffsrqr_destroy(kv.second.first);
   if (s->slot_info) cudaFreeHost(s->slot_info);
   if (s->arena_base) cudaFree(s->arena_base);

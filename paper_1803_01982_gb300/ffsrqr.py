@@ -132,6 +132,12 @@ def _load():
     lib.ffsrqr_batch_tune.restype = ctypes.c_int
     lib.ffsrqr_batch_streams.argtypes = [P]
     lib.ffsrqr_batch_streams.restype = ctypes.c_int
+    lib.ffsrqr_batch_set_phased.argtypes = [P, i32]
+    lib.ffsrqr_batch_set_phased.restype = ctypes.c_int
+    lib.ffsrqr_batch_phased.argtypes = [P]
+    lib.ffsrqr_batch_phased.restype = ctypes.c_int
+    lib.ffsrqr_batch_small_svd_launches.argtypes = [P]
+    lib.ffsrqr_batch_small_svd_launches.restype = ctypes.c_int
     lib.ffsrqr_batch_workspace_offset.argtypes = [P, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(P)]
     lib.ffsrqr_batch_workspace_offset.restype = ctypes.c_int
     lib.ffsrqr_batch_destroy.argtypes = [P]
@@ -149,6 +155,12 @@ def _load():
     lib.ffsrqr_server_stats.restype = ctypes.c_int
     lib.ffsrqr_server_destroy.argtypes = [P]
     lib.ffsrqr_server_destroy.restype = ctypes.c_int
+    lib.ffsrqr_server_set_phase_batch.argtypes = [P, i32]
+    lib.ffsrqr_server_set_phase_batch.restype = ctypes.c_int
+    lib.ffsrqr_server_pause.argtypes = [P, i32]
+    lib.ffsrqr_server_pause.restype = ctypes.c_int
+    lib.ffsrqr_server_phase_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ffsrqr_server_phase_stats.restype = ctypes.c_int
     lib.ffsrqr_pipe_create.argtypes = [ctypes.POINTER(P), P, ctypes.POINTER(ctypes.c_size_t)]
     lib.ffsrqr_pipe_create.restype = ctypes.c_int
     lib.ffsrqr_pipe_run.argtypes = [P, ctypes.POINTER(HostProblem), i32, P, P, P, ctypes.POINTER(Info)]
@@ -199,6 +211,9 @@ ffsrqr_batch_create = lib.ffsrqr_batch_create
 ffsrqr_batch_run = lib.ffsrqr_batch_run
 ffsrqr_batch_tune = lib.ffsrqr_batch_tune
 ffsrqr_batch_streams = lib.ffsrqr_batch_streams
+ffsrqr_batch_set_phased = lib.ffsrqr_batch_set_phased
+ffsrqr_batch_phased = lib.ffsrqr_batch_phased
+ffsrqr_batch_small_svd_launches = lib.ffsrqr_batch_small_svd_launches
 ffsrqr_batch_workspace_offset = lib.ffsrqr_batch_workspace_offset
 ffsrqr_batch_destroy = lib.ffsrqr_batch_destroy
 ffsrqr_server_create = lib.ffsrqr_server_create
@@ -207,6 +222,9 @@ ffsrqr_server_poll = lib.ffsrqr_server_poll
 ffsrqr_server_wait = lib.ffsrqr_server_wait
 ffsrqr_server_stats = lib.ffsrqr_server_stats
 ffsrqr_server_destroy = lib.ffsrqr_server_destroy
+ffsrqr_server_set_phase_batch = lib.ffsrqr_server_set_phase_batch
+ffsrqr_server_pause = lib.ffsrqr_server_pause
+ffsrqr_server_phase_stats = lib.ffsrqr_server_phase_stats
 ffsrqr_qrcp_static = lib.ffsrqr_qrcp_static
 ffsrqr_pipe_create = lib.ffsrqr_pipe_create
 ffsrqr_pipe_run = lib.ffsrqr_pipe_run
@@ -453,6 +471,18 @@ class Batch:
                                      ctypes.byref(chosen), ctypes.byref(ms)), "ffsrqr_batch_tune")
         return chosen.value, ms.value
 
+    def set_phased(self, phased: bool):
+        """Phase-batched graph: the small SVDs of all single-precision problems in
+        one launch per cluster size (ffsrqr_batch_set_phased)."""
+        _check(lib.ffsrqr_batch_set_phased(self._h, 1 if phased else 0), "ffsrqr_batch_set_phased")
+
+    @property
+    def phased(self) -> bool:
+        return lib.ffsrqr_batch_phased(self._h) == 1
+
+    def small_svd_launches(self) -> int:
+        return lib.ffsrqr_batch_small_svd_launches(self._h)
+
     def info(self, i: int) -> dict:
         sz = ctypes.sizeof(Info)
         return Info.from_buffer_copy(bytes(self._info[i * sz:(i + 1) * sz].numpy().tobytes())).as_dict()
@@ -504,6 +534,20 @@ class Server:
         _check(lib.ffsrqr_server_stats(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(q), ctypes.byref(f)),
                "ffsrqr_server_stats")
         return {"admitted": a.value, "completed": c.value, "queued": q.value, "arena_free": f.value}
+
+    def set_phase_batch(self, on: bool):
+        """Same-phase batching of the small SVDs (ffsrqr_server_set_phase_batch)."""
+        _check(lib.ffsrqr_server_set_phase_batch(self._h, 1 if on else 0), "ffsrqr_server_set_phase_batch")
+
+    def pause(self, paused: bool):
+        """Hold (True) or resume (False) admission (ffsrqr_server_pause)."""
+        _check(lib.ffsrqr_server_pause(self._h, 1 if paused else 0), "ffsrqr_server_pause")
+
+    def phase_stats(self) -> dict:
+        nl, nr = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.ffsrqr_server_phase_stats(self._h, ctypes.byref(nl), ctypes.byref(nr)),
+               "ffsrqr_server_phase_stats")
+        return {"small_svd_launches": nl.value, "grouped_requests": nr.value}
 
     def close(self):
         if self._h.value:

@@ -1,8 +1,10 @@
 """Batched problems as one CUDA graph (ffsrqr_batch_*): every problem's result
 equals its standalone ffsrqr_run bit for bit (the same kernels in the same
 order on its own workspace slice, whichever stream the graph gives it), on
-the first (captured) and later (replayed) launches and after the stream-count
-autotuner; one problem is also checked against the FP64 oracle."""
+the first (captured) and later (replayed) launches and after the
+autotuner; one problem is also checked against the FP64 oracle.  In the
+phase-batched graph the small SVDs of all problems run in one launch per
+thread-block-cluster size, again bitwise as standalone."""
 import numpy as np
 import pytest
 
@@ -80,3 +82,31 @@ def test_batch_autotune_and_oracle():
     so = oracle.ffsrqr(A, k, p, seed=0)
     S = outs[0][1].double().cpu().numpy()
     assert np.all(np.abs(S - so.S) <= 2e-5 * so.S[0] + 1e-5 * so.S)
+
+
+@pytest.mark.parametrize("mode", [ffsrqr.PLAIN_FP32, ffsrqr.MIXED_BF16X3])
+def test_phase_batched_graph_equals_standalone(mode):
+    sizes, mats = uneven_problems(9, seed=21)
+    # one problem with k > 64 (an 8-block cluster) beside the k <= 40 ones
+    # (2- and 4-block clusters): three cluster sizes, three batched launches
+    A = synth.decayed(1500, 1204, 0.97 ** np.arange(1204), 1e-4, seed=77)
+    sizes.append((1500, 1204, 80, 10))
+    mats.append(torch.as_tensor(A).cuda())
+    ks = [sz[2] for sz in sizes]
+    clusters = {8 if k > 64 else (4 if k > 16 else 2) for k in ks}
+    ref = standalone(sizes, mats, mode)
+    b = ffsrqr.Batch(sizes, mode, streams=4)
+    b.set_phased(True)
+    assert b.phased
+    outs = b.outputs()
+    for launch in range(2):  # capture, then replay
+        for o in outs:
+            for t in o:
+                t.zero_()
+        b.run(mats, outs)
+        torch.cuda.synchronize()
+        assert b.small_svd_launches() == len(clusters)
+        for i, (o, r) in enumerate(zip(outs, ref)):
+            for got, exp in zip(o, r):
+                assert torch.equal(got.cpu(), exp), (launch, i)
+            assert b.info(i)["status"] == 0

@@ -80,3 +80,29 @@ def test_request_beyond_budget_is_refused():
     with pytest.raises(ffsrqr.FfsrqrError, match="returned 5"):
         srv.submit(A, 50, 10, ffsrqr.PLAIN_FP32, outputs_for(A, 50))
     srv.close()
+
+
+@pytest.mark.parametrize("mode", [ffsrqr.PLAIN_FP32, ffsrqr.MIXED_BF16X3])
+def test_same_phase_batching_shares_small_svd_launches(mode):
+    # six requests submitted while admission is held are admitted in one pass;
+    # with same-phase batching their small SVDs run in one launch per
+    # thread-block-cluster size (k = r + 10 in [20, 50]: 4-block clusters, one
+    # launch), and every result is still bitwise the request run alone
+    reqs = svt_like_requests(6, seed=8)
+    ref = [alone(A, k, p, mode) for A, k, p in reqs]
+    srv = ffsrqr.Server(8 << 30, slots=6)
+    srv.set_phase_batch(True)
+    srv.pause(True)
+    outs = [outputs_for(A, k) for A, k, _ in reqs]
+    tickets = [srv.submit(A, k, p, mode, o) for (A, k, p), o in zip(reqs, outs)]
+    srv.pause(False)
+    results = [srv.wait(t) for t in tickets]
+    ph = srv.phase_stats()
+    srv.close()
+    assert ph["grouped_requests"] == 6, ph
+    clusters = {8 if k > 64 else (4 if k > 16 else 2) for _, k, _ in reqs}
+    assert ph["small_svd_launches"] == len(clusters), ph
+    for (info, lat), o, r in zip(results, outs, ref):
+        assert info["status"] == 0 and lat > 0
+        for got, exp in zip(o, r):
+            assert torch.equal(got.cpu(), exp)
