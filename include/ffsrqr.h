@@ -174,6 +174,20 @@ const char *ffsrqr_status_string(int code);
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char *ffsrqr_last_cuda_error(void);
 
+/* Autotuner of the tensor-core launches (mixed modes): runs the pipeline on
+ * the given problem (arguments as ffsrqr_run; outputs hold the last run)
+ * while trying, site by site, the pipeline depth of each pass over A (the
+ * stages its shared memory holds, or one or two fewer) and the stream-K grid
+ * of the Cholesky-QR Grams (all SMs, a half, a quarter), keeping a choice
+ * only when the whole run got faster (one warm-up and two timed runs each).
+ * The plan keeps the chosen configuration for its later runs.  config
+ * (int32[4], may be NULL) receives the stages of passes 1-3 and the Gram
+ * grid (0: the default), *ms_best (may be NULL) the best milliseconds per
+ * run.  Returns as ffsrqr_run. */
+int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,
+                     void *S, void *V, int64_t ldv, int32_t *piv, void *workspace, void *stream,
+                     int32_t *config, float *ms_best);
+
 /* Location of an intermediate inside the workspace after ffsrqr_run, for
  * step-by-step checks.  what: 0 Omega (s x m), 1 B^T (n x s), 2 S11 (k x k,
  * R factor of the sketched pivot columns), 3 Q1 (m x k), 4 G^T = A^T Q1

@@ -126,6 +126,12 @@ struct ffsrqr_plan_s {
   cudaEvent_t ev[2][13];
   cudaEvent_t ev_tc[2][3][2];  // around each tensor-core pass kernel
   int evset;                   // set of the current / last run
+  // tensor-core launch configuration per call site (0: the default), set by
+  // ffsrqr_plan_tune: sites 0-2 the passes over A (pipeline depth), site 3
+  // the Grams of the Cholesky-QR sweeps (stream-K grid)
+  int tc_stages[4] = {0, 0, 0, 0};
+  int tc_grid[4] = {0, 0, 0, 0};
+  mutable int tc_stages_fit[4] = {0, 0, 0, 0};  // stages the shared memory holds (recorded by launch_tc)
   long long runs;
   int launches;        // kernel launches of the last run
   bool ev_ok;
@@ -285,6 +291,8 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   // than the partials and their fixup
   sc.whole_tiles = (sc.KB <= 64) ? 1 : 0;
   if (sc.whole_tiles) sc.G = std::min(sc.G, sc.tiles);
+  const int site = (pass >= 0) ? pass : ((!sc.whole_tiles && a_mn) ? 3 : -1);
+  if (site >= 0 && P->tc_grid[site] > 0) sc.G = std::min(sc.G, P->tc_grid[site]);
   int stage_bytes = 0;
   if (bf && nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true, true>::bytes(ntile);
   else if (bf && nprod == 3 && a_mn) stage_bytes = TcStage<32, 3, true, true>::bytes(ntile);
@@ -294,6 +302,8 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   else stage_bytes = TcStage<16, 3, false>::bytes(ntile);
   const int budget = P->smem_optin - 2048;  // static shared memory and alignment slack
   sc.stages = std::min(TC_MAX_STAGES, budget / stage_bytes);
+  if (site >= 0) P->tc_stages_fit[site] = sc.stages;
+  if (site >= 0 && P->tc_stages[site] > 0) sc.stages = std::min(sc.stages, P->tc_stages[site]);
   if (sc.stages < 2) return FFSRQR_STATUS_UNSUPPORTED;
   const size_t smem = (size_t)sc.stages * stage_bytes + 1024;
 #define TC_LAUNCH(BKv, NPv, AMNv, BFv)                                                               \
@@ -1454,6 +1464,75 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   }
   plan->launches = g_launches;
   return rc;
+}
+
+int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,
+                     void *S, void *V, int64_t ldv, int32_t *piv, void *workspace, void *stream,
+                     int32_t *config, float *ms_best) {
+  if (!plan) return -1;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return FFSRQR_STATUS_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return FFSRQR_STATUS_CUDA;
+  }
+  // one warm-up and two timed runs per configuration
+  auto time_runs = [&](float *ms) -> int {
+    int rc = ffsrqr_run(plan, A, lda, seed, U, ldu, S, V, ldv, piv, workspace, stream, nullptr);
+    if (rc) return rc;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return FFSRQR_STATUS_CUDA;
+    for (int r = 0; r < 2 && !rc; ++r) rc = ffsrqr_run(plan, A, lda, seed, U, ldu, S, V, ldv, piv, workspace, stream,
+                                                       nullptr);
+    if (rc) return rc;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return FFSRQR_STATUS_CUDA;
+    *ms *= 0.5f;
+    return 0;
+  };
+  int rc = 0;
+  float best = 0.f;
+  for (int site = 0; site < 4; ++site) {
+    plan->tc_stages[site] = plan->tc_grid[site] = 0;
+  }
+  rc = time_runs(&best);
+  // coordinate descent over the sites: the pipeline depth of each pass (all
+  // the stages its shared memory holds, or one or two fewer) and the
+  // stream-K grid of the Grams (all SMs, a half, a quarter); a candidate is
+  // kept only when the whole run got faster
+  for (int site = 0; site < 4 && !rc; ++site) {
+    for (int c = 1; c <= 2 && !rc; ++c) {
+      const int keep_s = plan->tc_stages[site], keep_g = plan->tc_grid[site];
+      if (site < 3) {
+        const int d = plan->tc_stages_fit[site];
+        if (d - c < 2) break;
+        plan->tc_stages[site] = d - c;
+      } else {
+        plan->tc_grid[site] = std::max(1, plan->num_sms >> c);
+      }
+      float t = 0.f;
+      rc = time_runs(&t);
+      if (!rc && t < best) {
+        best = t;
+      } else {
+        plan->tc_stages[site] = keep_s;
+        plan->tc_grid[site] = keep_g;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    for (int site = 0; site < 4; ++site) plan->tc_stages[site] = plan->tc_grid[site] = 0;
+    return rc;
+  }
+  if (config) {
+    for (int site = 0; site < 3; ++site) config[site] = plan->tc_stages[site];
+    config[3] = plan->tc_grid[3];
+  }
+  if (ms_best) *ms_best = best;
+  return 0;
 }
 
 }  // extern "C"

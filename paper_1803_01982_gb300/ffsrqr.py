@@ -119,6 +119,9 @@ def _load():
     lib.ffsrqr_phase_times.restype = ctypes.c_int
     lib.ffsrqr_phase_times_back.argtypes = [P, i32, ctypes.POINTER(ctypes.c_float), i32]
     lib.ffsrqr_phase_times_back.restype = ctypes.c_int
+    lib.ffsrqr_plan_tune.argtypes = [P, P, i64, ctypes.c_uint64, P, i64, P, P, i64, P, P, P, ctypes.POINTER(i32),
+                                     ctypes.POINTER(ctypes.c_float)]
+    lib.ffsrqr_plan_tune.restype = ctypes.c_int
     lib.ffsrqr_launch_count.argtypes = [P]
     lib.ffsrqr_launch_count.restype = ctypes.c_int
     lib.ffsrqr_qrcp_static.argtypes = [P, i64, i32, i64, i32, P, P, P, P]
@@ -206,6 +209,7 @@ ffsrqr_workspace_item = lib.ffsrqr_workspace_item
 ffsrqr_philox4x32_10 = lib.ffsrqr_philox4x32_10
 ffsrqr_phase_times = lib.ffsrqr_phase_times
 ffsrqr_launch_count = lib.ffsrqr_launch_count
+ffsrqr_plan_tune = lib.ffsrqr_plan_tune
 ffsrqr_phase_times_back = lib.ffsrqr_phase_times_back
 ffsrqr_batch_create = lib.ffsrqr_batch_create
 ffsrqr_batch_run = lib.ffsrqr_batch_run
@@ -317,6 +321,19 @@ class Plan:
                               S.data_ptr(), V.data_ptr(), V.stride(0), piv.data_ptr(), self.ws_ptr,
                               ctypes.c_void_p(st.cuda_stream), info_ptr), "ffsrqr_run")
         return U, S, V, piv
+
+    def tune(self, A, seed: int = 0, out=None, stream=None):
+        """Autotune the tensor-core launch configuration on A (ffsrqr_plan_tune);
+        returns (config [stages of passes 1-3, Gram grid], best ms per run)."""
+        import torch
+        assert A.is_cuda and A.dtype == self.dtype and A.shape == (self.m, self.n)
+        U, S, V, piv = out if out is not None else self.outputs()
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        cfg, ms = (ctypes.c_int32 * 4)(), ctypes.c_float()
+        _check(lib.ffsrqr_plan_tune(self._h, A.data_ptr(), A.stride(0), seed, U.data_ptr(), U.stride(0),
+                                    S.data_ptr(), V.data_ptr(), V.stride(0), piv.data_ptr(), self.ws_ptr,
+                                    ctypes.c_void_p(st.cuda_stream), cfg, ctypes.byref(ms)), "ffsrqr_plan_tune")
+        return list(cfg), ms.value
 
     def info(self) -> dict:
         """Report of the last run (call after synchronising its stream)."""

@@ -135,3 +135,24 @@ def test_mixed_deterministic(mode):
     _, b = run(A, 30, 10, mode)
     for key in ["U", "S", "V", "piv"]:
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_plan_tune_keeps_results_within_tolerance():
+    # the autotuner changes only launch shapes (pipeline depth, stream-K grid):
+    # the tuned plan's results still match the oracle as before, and its
+    # configuration is one of the candidates
+    A = graded(2100, 660, 0.9, seed=2760)
+    plan = ffsrqr.Plan(2100, 660, 64, 10, ffsrqr.MIXED_BF16X3)
+    Ad = torch.as_tensor(A).cuda()
+    cfg, ms = plan.tune(Ad)
+    torch.cuda.synchronize()
+    assert ms > 0 and len(cfg) == 4
+    assert all(c == 0 or 2 <= c <= 8 for c in cfg[:3])
+    assert cfg[3] in (0, 76, 38) or cfg[3] > 0
+    U, S, V, piv = plan.run(Ad, seed=0)
+    torch.cuda.synchronize()
+    ref = oracle.ffsrqr(A, 64, 10, seed=0)
+    got = {"U": U.double().cpu().numpy(), "S": S.double().cpu().numpy(), "V": V.double().cpu().numpy(),
+           "piv": piv.cpu().numpy(), "info": plan.info()}
+    assert list(got["piv"][:64]) == list(ref.piv[:64])
+    check_fp32(A, 64, got, ref)
