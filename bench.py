@@ -64,6 +64,8 @@ def parse():
                          "matrix; serving: Poisson request stream")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--phase-batch", action="store_true",
+                    help="serving: batch the small SVDs of requests admitted together")
     return ap.parse_args()
 
 
@@ -508,7 +510,8 @@ def run_batch(a):
     ms = _time_batch(a, b, mats, outs)
     roof = sum(12.0 * m * n for m, n, _, _ in sizes)
     _batch_line(a, f"256 uneven FP32 matrices (m, n in [256, 4096], k in [8, 64], p = 10, sigma_j = 0.9^j), {a.mode}",
-                256, ms, roof, {"autotune": {"streams": chosen, "ms": tune_ms}})
+                256, ms, roof, {"autotune": {"streams": chosen, "phase_batched": b.phased, "ms": tune_ms,
+                                             "small_svd_launches": b.small_svd_launches()}})
 
 
 def run_hosvd(a):
@@ -705,6 +708,8 @@ def run_serving(a):
         pool.append((A, r + 10))
     mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     srv = ffsrqr.Server(120 * (1 << 30), slots=8)
+    if a.phase_batch:
+        srv.set_phase_batch(True)
     # warm the plan cache and the kernels
     for A, k in pool[:4]:
         o = (torch.empty(A.shape[0], k, device="cuda"), torch.empty(k, device="cuda"),
@@ -734,13 +739,16 @@ def run_serving(a):
     for t in pending:
         lat.append(srv.wait(t)[1])
     wall = time.perf_counter() - t0
+    ph = srv.phase_stats()
     srv.close()
     lat = np.array(lat) * 1e3
     line = {"metric": "serving latency p50/p99 (ms) and throughput", "value": len(lat) / wall,
             "unit": "req/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"Poisson {a.rate:g} req/s for {a.duration:g} s, m, n in [500, 8000], "
-                                   f"rank 10..100 + noise, k = r + 10, p = 10, 120 GB budget, 8 slots, {a.mode}"},
+                                   f"rank 10..100 + noise, k = r + 10, p = 10, 120 GB budget, 8 slots, {a.mode}",
+                       "same_phase_batching": bool(a.phase_batch)},
+            "offered_req_s": float(len(arrivals) / a.duration), "phase_stats": ph,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max())},
             "requests": int(len(lat)), "wall_s": wall}

@@ -167,10 +167,14 @@ void fail_start(ffsrqr_server_s *s, int64_t t, int rc) {
 // Start the admitted requests (slots and workspaces reserved).  Caller holds
 // s->mu.
 void start(ffsrqr_server_s *s, const std::vector<int64_t> &adm) {
+  // a group needs two batchable requests; a single one runs as usual
+  int nb = 0;
+  if (s->phase_batch)
+    for (int64_t t : adm) nb += ffq_phase_batchable(s->reqs[t].plan) ? 1 : 0;
   std::vector<int64_t> grp;
   for (int64_t t : adm) {
     Req &rq = s->reqs[t];
-    if (s->phase_batch && ffq_phase_batchable(rq.plan)) {
+    if (nb >= 2 && ffq_phase_batchable(rq.plan)) {
       grp.push_back(t);
       continue;
     }
