@@ -176,14 +176,16 @@ const char *ffsrqr_last_cuda_error(void);
 
 /* Autotuner of the tensor-core launches (mixed modes): runs the pipeline on
  * the given problem (arguments as ffsrqr_run; outputs hold the last run)
- * while trying, site by site, the pipeline depth of each pass over A (the
- * stages its shared memory holds, or one or two fewer) and the stream-K grid
- * of the Cholesky-QR Grams (all SMs, a half, a quarter), keeping a choice
- * only when the whole run got faster (one warm-up and two timed runs each).
- * The plan keeps the chosen configuration for its later runs.  config
- * (int32[4], may be NULL) receives the stages of passes 1-3 and the Gram
- * grid (0: the default), *ms_best (may be NULL) the best milliseconds per
- * run.  Returns as ffsrqr_run. */
+ * while trying, site by site, the schedule of each pass over A (whole tiles
+ * data-parallel first, the default, or all stream-K), its pipeline depth
+ * (the stages its shared memory holds, or one or two fewer) and the
+ * stream-K grid of the Cholesky-QR Grams (all SMs, a half, a quarter),
+ * keeping a choice only when the whole run got faster (one warm-up and two
+ * timed runs each).  The plan keeps the chosen configuration for its later
+ * runs.  config (int32[7], may be NULL) receives the stages of passes 1-3,
+ * the Gram grid (0: the default) and, for passes 1-3, 1 where all stream-K
+ * was chosen; *ms_best (may be NULL) the best milliseconds per run.
+ * Returns as ffsrqr_run. */
 int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,
                      void *S, void *V, int64_t ldv, int32_t *piv, void *workspace, void *stream,
                      int32_t *config, float *ms_best);

@@ -131,6 +131,7 @@ struct ffsrqr_plan_s {
   // the Grams of the Cholesky-QR sweeps (stream-K grid)
   int tc_stages[4] = {0, 0, 0, 0};
   int tc_grid[4] = {0, 0, 0, 0};
+  int tc_sk[4] = {0, 0, 0, 0};  // 1: all stream-K (no data-parallel tiles first)
   mutable int tc_stages_fit[4] = {0, 0, 0, 0};  // stages the shared memory holds (recorded by launch_tc)
   long long runs;
   int launches;        // kernel launches of the last run
@@ -284,8 +285,6 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   sc.part = reinterpret_cast<float *>(ws + P->off_tcpart);
   sc.ctl = reinterpret_cast<int *>(ws + P->off_ctl);
   sc.vec4 = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0);
-  // few tiles shared by many blocks (a Gram): one row per fixup block
-  sc.fix_rows = (8LL * sc.tiles < sc.G) ? 1 : 4;
   // short K (a tall matrix times a k x k factor): whole tiles per block,
   // written directly, no fixup; the extra tile some blocks take costs less
   // than the partials and their fixup
@@ -293,6 +292,15 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   if (sc.whole_tiles) sc.G = std::min(sc.G, sc.tiles);
   const int site = (pass >= 0) ? pass : ((!sc.whole_tiles && a_mn) ? 3 : -1);
   if (site >= 0 && P->tc_grid[site] > 0) sc.G = std::min(sc.G, P->tc_grid[site]);
+  // data-parallel whole tiles first (a multiple of G), stream-K on the rest,
+  // when the rest gives every block at least one unit (else all stream-K)
+  sc.dpt = 0;
+  if (!sc.whole_tiles && sc.tiles >= sc.G && !(site >= 0 && P->tc_sk[site])) {
+    const int rest = sc.tiles % sc.G;
+    if (rest == 0 || (long long)rest * sc.KB >= sc.G) sc.dpt = sc.tiles - rest;
+  }
+  // few stream-K tiles shared by many blocks (a Gram): one row per fixup block
+  sc.fix_rows = (8LL * (sc.tiles - sc.dpt) < sc.G) ? 1 : 4;
   int stage_bytes = 0;
   if (bf && nprod == 1 && a_mn) stage_bytes = TcStage<32, 1, true, true>::bytes(ntile);
   else if (bf && nprod == 3 && a_mn) stage_bytes = TcStage<32, 3, true, true>::bytes(ntile);
@@ -323,8 +331,8 @@ int launch_tc(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int pa
   else return FFSRQR_STATUS_UNSUPPORTED;
 #undef TC_LAUNCH
   CKL("tc_gemm");
-  if (!sc.whole_tiles) {
-    tc_fixup_kernel<<<dim3(sc.tiles, TC_BM / sc.fix_rows), 256, 0, st>>>(sc);
+  if (!sc.whole_tiles && sc.dpt < sc.tiles) {
+    tc_fixup_kernel<<<dim3(sc.tiles - sc.dpt, TC_BM / sc.fix_rows), 256, 0, st>>>(sc);
     CKL("tc_fixup");
   }
   return 0;
@@ -1493,14 +1501,20 @@ int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t se
   };
   int rc = 0;
   float best = 0.f;
-  for (int site = 0; site < 4; ++site) {
-    plan->tc_stages[site] = plan->tc_grid[site] = 0;
-  }
+  for (int site = 0; site < 4; ++site) plan->tc_stages[site] = plan->tc_grid[site] = plan->tc_sk[site] = 0;
   rc = time_runs(&best);
-  // coordinate descent over the sites: the pipeline depth of each pass (all
-  // the stages its shared memory holds, or one or two fewer) and the
+  // coordinate descent over the sites: for each pass over A the schedule
+  // (data-parallel tiles first, or all stream-K) and the pipeline depth (all
+  // the stages its shared memory holds, or one or two fewer), and the
   // stream-K grid of the Grams (all SMs, a half, a quarter); a candidate is
   // kept only when the whole run got faster
+  for (int site = 0; site < 3 && !rc; ++site) {
+    plan->tc_sk[site] = 1;
+    float t = 0.f;
+    rc = time_runs(&t);
+    if (!rc && t < best) best = t;
+    else plan->tc_sk[site] = 0;
+  }
   for (int site = 0; site < 4 && !rc; ++site) {
     for (int c = 1; c <= 2 && !rc; ++c) {
       const int keep_s = plan->tc_stages[site], keep_g = plan->tc_grid[site];
@@ -1524,12 +1538,13 @@ int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t se
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) {
-    for (int site = 0; site < 4; ++site) plan->tc_stages[site] = plan->tc_grid[site] = 0;
+    for (int site = 0; site < 4; ++site) plan->tc_stages[site] = plan->tc_grid[site] = plan->tc_sk[site] = 0;
     return rc;
   }
   if (config) {
     for (int site = 0; site < 3; ++site) config[site] = plan->tc_stages[site];
     config[3] = plan->tc_grid[3];
+    for (int site = 0; site < 3; ++site) config[4 + site] = plan->tc_sk[site];
   }
   if (ms_best) *ms_best = best;
   return 0;

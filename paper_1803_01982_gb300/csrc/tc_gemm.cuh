@@ -47,11 +47,14 @@
 // memory; D = Ah Bh + Ah Bl + Al Bh with FP32 accumulation (about 2^-16 per
 // product).  The one-product BF16 sketch keeps the head only.
 //
-// Stream-K: unit u = tile*KB + kb; block c owns units [U*c/G, U*(c+1)/G).  A
-// block's first and last segments may cover part of a tile's K range; those
-// partial tiles go to part[(2c + slot)] and tc_fixup_kernel adds the pieces of
-// each tile in block order (deterministic).  All other tiles are written
-// directly.  With a short K (sc.whole_tiles) block c owns the whole tiles
+// Schedule (unit u = tile*KB + kb): the first dpt = tiles - tiles mod G tiles
+// are data-parallel, block c taking dpt/G consecutive whole tiles; the last
+// tiles mod G tiles are stream-K over all blocks, block c owning their units
+// [S*c/G, S*(c+1)/G) (S of them).  A block's first and last stream-K
+// segments may cover part of a tile's K range; those partial tiles go to
+// part[(2c + slot)] and tc_fixup_kernel adds the pieces of each such tile in
+// block order (deterministic).  All other tiles are written directly.  (With
+// fewer tiles than blocks, a Gram, everything is stream-K.)  With a short K (sc.whole_tiles) block c owns the whole tiles
 // [tiles*c/G, tiles*(c+1)/G) instead: every tile is written directly and no
 // fixup runs.  Every mbarrier wait is bounded (~1 s); on expiry the block
 // records STATUS_TIMEOUT, drains what it issued, frees its TMEM and exits.
@@ -102,6 +105,7 @@ struct TcSched {
   int vec4;         // C rows are 16-byte aligned (C % 16 == 0, ldc % 4 == 0)
   int fix_rows;     // rows of a tile per fixup block (divides TC_BM)
   int whole_tiles;  // 1: block c takes tiles [tiles c / G, tiles (c+1) / G) whole (no partials)
+  int dpt;          // data-parallel tiles (a multiple of G; the rest are stream-K)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -245,16 +249,39 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Segment iterator shared by all roles: block c walks units [u0, u1).
+// Block c's units: range 0 its data-parallel tiles (or, with sc.whole_tiles,
+// its whole tiles), range 1 its stream-K units.
+__device__ __forceinline__ void tc_range(const TcSched &sc, int c, int r, int &a, int &b) {
+  if (sc.whole_tiles) {
+    a = (r == 0) ? (int)(((long long)sc.tiles * c) / sc.G) * sc.KB : 0;
+    b = (r == 0) ? (int)(((long long)sc.tiles * (c + 1)) / sc.G) * sc.KB : 0;
+  } else if (r == 0) {
+    const int per = (sc.dpt / sc.G) * sc.KB;
+    a = c * per;
+    b = a + per;
+  } else {
+    const long long base = (long long)sc.dpt * sc.KB, sk = sc.U - base;
+    a = (int)(base + (sk * c) / sc.G);
+    b = (int)(base + (sk * (c + 1)) / sc.G);
+  }
+}
+
+// Segment iterator shared by all roles: block c walks its range 0, then its
+// range 1 (units < 2^31); the second range is formed from the launch's
+// parameters when the first runs out, so a role holds only two counters.
 struct SegIter {
-  long long u, u1;
-  int KB;
-  __device__ bool next(int &tile, int &kb0, int &kb1) {
-    if (u >= u1) return false;
-    tile = (int)(u / KB);
-    kb0 = (int)(u - (long long)tile * KB);
-    const long long left = u1 - u;
-    kb1 = (int)((long long)kb0 + left < KB ? kb0 + left : KB);
+  int u, u1, r;
+  __device__ bool next(const TcSched &sc, int &tile, int &kb0, int &kb1) {
+    if (u >= u1) {
+      if (r != 0) return false;
+      r = 1;
+      tc_range(sc, (int)blockIdx.x, 1, u, u1);
+      if (u >= u1) return false;
+    }
+    tile = u / sc.KB;
+    kb0 = u - tile * sc.KB;
+    const int left = u1 - u;
+    kb1 = (kb0 + left < sc.KB) ? kb0 + left : sc.KB;
     u += kb1 - kb0;
     return true;
   }
@@ -377,15 +404,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x;
   SegIter it;
-  if (sc.whole_tiles) {
-    it.u = (long long)(((long long)sc.tiles * c) / sc.G) * sc.KB;
-    it.u1 = (long long)(((long long)sc.tiles * (c + 1)) / sc.G) * sc.KB;
-  } else {
-    it.u = (sc.U * c) / sc.G;
-    it.u1 = (sc.U * (c + 1)) / sc.G;
+  tc_range(sc, c, 0, it.u, it.u1);
+  it.r = 0;
+  int first_tile;  // the first stream-K tile (partial slot 0)
+  {
+    int a, b;
+    tc_range(sc, c, 1, a, b);
+    first_tile = a / sc.KB;
   }
-  it.KB = sc.KB;
-  const int first_tile = (int)(it.u / sc.KB);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -428,7 +454,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int tile, kb0, kb1;
     SegIter my = it;
     bool ok = true;
-    while (ok && my.next(tile, kb0, kb1)) {
+    while (ok && my.next(sc, tile, kb0, kb1)) {
       for (int kb = kb0; kb < kb1; ++kb) {
         if constexpr (BF) {
           // all converter warps take the same decision: leave together on a
@@ -557,7 +583,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         SegIter my = it;
         bool ok = true;
         uint32_t issued = 0, issued_ph = 0;  // per stage: a load in flight, and its phase parity
-        while (ok && my.next(tile, kb0, kb1)) {
+        while (ok && my.next(sc, tile, kb0, kb1)) {
           for (int kb = kb0; kb < kb1 && ok; ++kb) {
             if (!mbar_wait(&empty_bar[s], ph ^ 1u, abortp, sc.ctl)) {
               ok = false;
@@ -599,7 +625,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         SegIter my = it;
         const uint32_t IDESC = BF ? idesc_bf16(NT) : idesc_tf32(NT);
         bool ok = true;
-        while (ok && my.next(tile, kb0, kb1)) {
+        while (ok && my.next(sc, tile, kb0, kb1)) {
           for (int kc = kb0; kc < kb1 && ok; kc += CHUNK) {
             const int kc1 = (kb1 - kc > CHUNK) ? kc + CHUNK : kb1;
             const int b = chunk & 1;
@@ -673,7 +699,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int tile, kb0, kb1;
     SegIter my = it;
     bool ok = true;
-    while (ok && my.next(tile, kb0, kb1)) {
+    while (ok && my.next(sc, tile, kb0, kb1)) {
       float acc[NACC];
 #pragma unroll
       for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
@@ -747,20 +773,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 constexpr int TC_MAX_GRID = 1024;  // upper bound of the persistent grid (fixup slot table)
 
-// Sum the partial pieces of the tiles that several blocks share, in block
-// order (deterministic), and write them to C.  Grid (tiles, TC_BM /
-// sc.fix_rows): one block per sc.fix_rows rows of a tile.
+// Sum the partial pieces of the stream-K tiles that several blocks share, in
+// block order (deterministic), and write them to C.  Grid (tiles - dpt,
+// TC_BM / sc.fix_rows): one block per sc.fix_rows rows of a stream-K tile.
 __global__ void tc_fixup_kernel(TcSched sc) {
   __shared__ int s_lo, s_hi;
   __shared__ unsigned char s_slot[TC_MAX_GRID];
-  const int tile = blockIdx.x;
+  const int tile = sc.dpt + blockIdx.x;
+  const long long base = (long long)sc.dpt * sc.KB, sk = sc.U - base;
   if (threadIdx.x == 0) {
     const long long ua = (long long)tile * sc.KB, ub = ua + sc.KB - 1;
-    auto owner = [&](long long u) {
+    auto owner = [&](long long u) {  // the block whose stream-K units hold u
       long long lo = 0, hi = sc.G - 1;
       while (lo < hi) {
         const long long mid = (lo + hi + 1) / 2;
-        if ((sc.U * mid) / sc.G <= u) lo = mid;
+        if (base + (sk * mid) / sc.G <= u) lo = mid;
         else hi = mid - 1;
       }
       return (int)lo;
@@ -774,7 +801,7 @@ __global__ void tc_fixup_kernel(TcSched sc) {
   // slot of this tile in each contributor's partial buffer: 0 if it is the
   // contributor's first tile, else 1
   for (int cb = c_lo + threadIdx.x; cb <= c_hi; cb += blockDim.x)
-    s_slot[cb - c_lo] = (tile == (int)(((sc.U * cb) / sc.G) / sc.KB)) ? 0 : 1;
+    s_slot[cb - c_lo] = (tile == (int)((base + (sk * cb) / sc.G) / sc.KB)) ? 0 : 1;
   __syncthreads();
   const int r0 = blockIdx.y * sc.fix_rows;
   for (int e = threadIdx.x; e < sc.fix_rows * sc.N; e += blockDim.x) {

@@ -324,12 +324,13 @@ class Plan:
 
     def tune(self, A, seed: int = 0, out=None, stream=None):
         """Autotune the tensor-core launch configuration on A (ffsrqr_plan_tune);
-        returns (config [stages of passes 1-3, Gram grid], best ms per run)."""
+        returns (config [stages of passes 1-3, Gram grid, all-stream-K flags of
+        passes 1-3], best ms per run)."""
         import torch
         assert A.is_cuda and A.dtype == self.dtype and A.shape == (self.m, self.n)
         U, S, V, piv = out if out is not None else self.outputs()
         st = torch.cuda.current_stream(self.device) if stream is None else stream
-        cfg, ms = (ctypes.c_int32 * 4)(), ctypes.c_float()
+        cfg, ms = (ctypes.c_int32 * 7)(), ctypes.c_float()
         _check(lib.ffsrqr_plan_tune(self._h, A.data_ptr(), A.stride(0), seed, U.data_ptr(), U.stride(0),
                                     S.data_ptr(), V.data_ptr(), V.stride(0), piv.data_ptr(), self.ws_ptr,
                                     ctypes.c_void_p(st.cuda_stream), cfg, ctypes.byref(ms)), "ffsrqr_plan_tune")

@@ -146,9 +146,9 @@ def test_plan_tune_keeps_results_within_tolerance():
     Ad = torch.as_tensor(A).cuda()
     cfg, ms = plan.tune(Ad)
     torch.cuda.synchronize()
-    assert ms > 0 and len(cfg) == 4
+    assert ms > 0 and len(cfg) == 7
     assert all(c == 0 or 2 <= c <= 8 for c in cfg[:3])
-    assert cfg[3] in (0, 76, 38) or cfg[3] > 0
+    assert cfg[3] >= 0 and all(c in (0, 1) for c in cfg[4:])
     U, S, V, piv = plan.run(Ad, seed=0)
     torch.cuda.synchronize()
     ref = oracle.ffsrqr(A, 64, 10, seed=0)
