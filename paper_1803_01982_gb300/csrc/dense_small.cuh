@@ -110,6 +110,40 @@ __global__ void transpose_kernel(const T *__restrict__ Src, int64_t lds, int64_t
 // y (P + dP) = x with |dP| <= gamma_{k+1} |P|.
 // A warp solves R rows at a time; lane l owns columns l, l+32, ... (NS slots).
 // ---------------------------------------------------------------------------
+// The k x k factor of a row solve into shared memory, Ps[j k + c] =
+// Pm[j psi + c psj], with its reciprocal diagonal.  Contiguous rows (psj = 1)
+// or columns (psi = 1) are read along memory, eight loads in flight a thread,
+// so that the copy costs a few memory latencies rather than one per element.
+template <typename T>
+__device__ __forceinline__ void trsm_load_factor(T *Ps, T *dinv, const T *__restrict__ Pm, int64_t psi,
+                                                 int64_t psj, int k) {
+  const int n = k * k;
+  const bool rows = (psj == 1), cols = (psi == 1);
+  for (int e0 = threadIdx.x; e0 < n; e0 += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < n) {
+        const int a = e / k, b = e - a * k;  // memory order: element b of line a
+        if (rows) v[u] = Pm[(int64_t)a * psi + b];
+        else if (cols) v[u] = Pm[(int64_t)a * psj + b];
+        else v[u] = Pm[(int64_t)a * psi + (int64_t)b * psj];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < n) {
+        const int a = e / k, b = e - a * k;
+        if (cols) Ps[b * k + a] = v[u];  // line a is column a of P
+        else Ps[e] = v[u];
+      }
+    }
+  }
+  for (int j = threadIdx.x; j < k; j += blockDim.x) dinv[j] = T(1) / Pm[(int64_t)j * psi + (int64_t)j * psj];
+}
+
 template <typename T, int NS, int R, bool FWD>
 __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64_t ldx, int64_t M,
                                                         int k, const T *__restrict__ Pm,
@@ -118,11 +152,7 @@ __global__ void __launch_bounds__(512) trsm_rows_kernel(T *__restrict__ X, int64
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ps = reinterpret_cast<T *>(smem_raw);  // k x k, row-major, P(j, c) at Ps[j*k + c]
   T *dinv = Ps + (size_t)k * k;             // 1 / P(j, j)
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e / k, j = e - i * k;
-    Ps[e] = Pm[(int64_t)i * psi + (int64_t)j * psj];
-  }
-  for (int j = threadIdx.x; j < k; j += blockDim.x) dinv[j] = T(1) / Pm[(int64_t)j * psi + (int64_t)j * psj];
+  trsm_load_factor(Ps, dinv, Pm, psi, psj, k);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t ngroups = (M + R - 1) / R;
@@ -206,11 +236,7 @@ __global__ void __launch_bounds__(512) trsm_rows2_kernel(float *__restrict__ X, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *Ps = reinterpret_cast<float *>(smem_raw);  // k x k, row-major, P(j, c) at Ps[j*k + c]
   float *dinv = Ps + (size_t)k * k;                 // 1 / P(j, j)
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e / k, j = e - i * k;
-    Ps[e] = Pm[(int64_t)i * psi + (int64_t)j * psj];
-  }
-  for (int j = threadIdx.x; j < k; j += blockDim.x) dinv[j] = 1.f / Pm[(int64_t)j * psi + (int64_t)j * psj];
+  trsm_load_factor(Ps, dinv, Pm, psi, psj, k);
   __syncthreads();
   constexpr int R = 2 * RP;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;

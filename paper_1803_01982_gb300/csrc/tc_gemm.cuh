@@ -808,23 +808,23 @@ __global__ void tc_fixup_kernel(TcSched sc) {
     const int rr = r0 + e / sc.N, col = e % sc.N;
     const int row = tile * TC_BM + rr;
     if (row >= sc.M) continue;
-    // added in block order (deterministic); many contributors (a Gram): eight
-    // loads in flight at a time
+    // added in block order (deterministic); many contributors (a Gram):
+    // thirty-two loads in flight at a time
     float acc = 0.f;
     if (c_hi - c_lo < 7) {
       for (int cb = c_lo; cb <= c_hi; ++cb)
         acc += sc.part[((int64_t)(2 * cb + s_slot[cb - c_lo]) * TC_BM + rr) * sc.ntile + col];
     } else {
-      for (int cb0 = c_lo; cb0 <= c_hi; cb0 += 8) {
-        float pv[8];
+      for (int cb0 = c_lo; cb0 <= c_hi; cb0 += 32) {
+        float pv[32];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 32; ++u) {
           const int cb = cb0 + u;
           pv[u] = (cb <= c_hi) ? sc.part[((int64_t)(2 * cb + s_slot[cb - c_lo]) * TC_BM + rr) * sc.ntile + col]
                                : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 32; ++u)
           if (cb0 + u <= c_hi) acc += pv[u];
       }
     }
