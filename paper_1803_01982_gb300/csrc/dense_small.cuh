@@ -718,17 +718,24 @@ __global__ void srqr_g2_kernel(const T *__restrict__ npart, int nnp, const T *__
 // piv[k:n] = columns not in J, ascending (one block, chunked scan).
 __global__ void __launch_bounds__(1024) piv_rest_kernel(const int *__restrict__ sel, int64_t n, int k,
                                                         int32_t *__restrict__ piv) {
-  // tiles of blockDim.x consecutive columns; a block-wide exclusive scan of
-  // the "not selected" flags gives each unselected column its position
+  // tiles of 8 blockDim.x consecutive columns, eight per thread; a block-wide
+  // exclusive scan of the per-thread counts of unselected columns gives each
+  // of them its position
+  constexpr int E = 8;
   __shared__ int wsum[32];
   __shared__ int s_base;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) s_base = k;
   __syncthreads();
-  for (int64_t t0 = 0; t0 < n; t0 += blockDim.x) {
-    const int64_t i = t0 + threadIdx.x;
-    const int f = (i < n && sel[i] == 0) ? 1 : 0;
-    int x = f;  // inclusive warp scan
+  for (int64_t t0 = 0; t0 < n; t0 += (int64_t)E * blockDim.x) {
+    const int64_t i0 = t0 + (int64_t)threadIdx.x * E;
+    int f[E], cnt = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      f[e] = (i0 + e < n && sel[i0 + e] == 0) ? 1 : 0;
+      cnt += f[e];
+    }
+    int x = cnt;  // inclusive warp scan of the counts
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -747,8 +754,13 @@ __global__ void __launch_bounds__(1024) piv_rest_kernel(const int *__restrict__ 
     }
     __syncthreads();
     const int base = s_base;
-    const int pos = base + (w > 0 ? wsum[w - 1] : 0) + x - f;
-    if (f && pos < n) piv[pos] = (int32_t)i;
+    int pos = base + (w > 0 ? wsum[w - 1] : 0) + x - cnt;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (f[e]) {
+        if (pos < n) piv[pos] = (int32_t)(i0 + e);
+        ++pos;
+      }
     __syncthreads();
     if (threadIdx.x == 0) s_base = base + wsum[nw - 1];
     __syncthreads();
