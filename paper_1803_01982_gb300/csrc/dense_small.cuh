@@ -594,25 +594,57 @@ __global__ void __launch_bounds__(256) srqr_resid_kernel(const T *__restrict__ A
                                                          int64_t ldq, int k, const T *__restrict__ avec,
                                                          const int *ctl, T *__restrict__ z,
                                                          T *__restrict__ hpart) {
+  // a warp takes SR_ROWS rows at a time (their loads and warp sums
+  // interleave) and keeps its part of h = Q1^T z in registers (k <= 256)
+  constexpr int SR_ROWS = 4, NJ = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nwarp = blockDim.x >> 5;
-  T *as = reinterpret_cast<T *>(smem_raw);  // k
-  T *hw = as + k;                           // nwarp x k
+  T *hw = reinterpret_cast<T *>(smem_raw);  // nwarp x k (the first k entries hold a first)
   const int c = ctl[CTL_CAND];
   if (c == 0x7fffffff) return;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) as[j] = avec[j];
-  for (int j = threadIdx.x; j < nwarp * k; j += blockDim.x) hw[j] = T(0);
-  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T as[NJ], hacc[NJ];
+#pragma unroll
+  for (int u = 0; u < NJ; ++u) {
+    const int j = lane + 32 * u;
+    as[u] = (j < k) ? avec[j] : T(0);
+    hacc[u] = T(0);
+  }
   const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * rows_per, i1 = min(m, i0 + rows_per);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t i = i0 + wid; i < i1; i += nwarp) {
-    T acc = T(0);
-    for (int j = lane; j < k; j += 32) acc = fma(Q1[i * ldq + j], as[j], acc);
-    acc = warp_sum(acc);
-    const T zi = A[i * lda + c] - acc;
-    if (lane == 0) z[i] = zi;
-    for (int j = lane; j < k; j += 32) hw[wid * k + j] = fma(Q1[i * ldq + j], zi, hw[wid * k + j]);
+  for (int64_t base = i0 + (int64_t)wid * SR_ROWS; base < i1; base += (int64_t)nwarp * SR_ROWS) {
+    T q[SR_ROWS][NJ], acc[SR_ROWS], ac[SR_ROWS];
+#pragma unroll
+    for (int r = 0; r < SR_ROWS; ++r) {
+      const int64_t i = base + r;
+      acc[r] = T(0);
+      ac[r] = (i < i1) ? A[i * lda + c] : T(0);
+#pragma unroll
+      for (int u = 0; u < NJ; ++u) {
+        const int j = lane + 32 * u;
+        q[r][u] = (i < i1 && j < k) ? Q1[i * ldq + j] : T(0);
+        acc[r] = fma(q[r][u], as[u], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < SR_ROWS; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+#pragma unroll
+    for (int r = 0; r < SR_ROWS; ++r) {
+      const int64_t i = base + r;
+      if (i < i1) {
+        const T zi = ac[r] - acc[r];
+        if (lane == 0) z[i] = zi;
+#pragma unroll
+        for (int u = 0; u < NJ; ++u) hacc[u] = fma(q[r][u], zi, hacc[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NJ; ++u) {
+    const int j = lane + 32 * u;
+    if (j < k) hw[wid * k + j] = hacc[u];
   }
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
@@ -629,6 +661,7 @@ __global__ void __launch_bounds__(256) srqr_reorth_kernel(int64_t m, const T *__
                                                           const T *__restrict__ hpart, int nhp,
                                                           const int *ctl, T *__restrict__ z,
                                                           T *__restrict__ npart) {
+  constexpr int SR_ROWS = 4, NJ = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *hs = reinterpret_cast<T *>(smem_raw);
   __shared__ T red[32];
@@ -639,18 +672,43 @@ __global__ void __launch_bounds__(256) srqr_reorth_kernel(int64_t m, const T *__
     hs[j] = acc;
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  T hv[NJ];
+#pragma unroll
+  for (int u = 0; u < NJ; ++u) {
+    const int j = lane + 32 * u;
+    hv[u] = (j < k) ? hs[j] : T(0);
+  }
   const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * rows_per, i1 = min(m, i0 + rows_per);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   T nacc = T(0);
-  for (int64_t i = i0 + wid; i < i1; i += nwarp) {
-    T acc = T(0);
-    for (int j = lane; j < k; j += 32) acc = fma(Q1[i * ldq + j], hs[j], acc);
-    acc = warp_sum(acc);
-    const T zi = z[i] - acc;
-    if (lane == 0) {
-      z[i] = zi;
-      nacc = fma(zi, zi, nacc);
+  for (int64_t base = i0 + (int64_t)wid * SR_ROWS; base < i1; base += (int64_t)nwarp * SR_ROWS) {
+    T acc[SR_ROWS], zz[SR_ROWS];
+#pragma unroll
+    for (int r = 0; r < SR_ROWS; ++r) {
+      const int64_t i = base + r;
+      acc[r] = T(0);
+      zz[r] = (i < i1) ? z[i] : T(0);
+#pragma unroll
+      for (int u = 0; u < NJ; ++u) {
+        const int j = lane + 32 * u;
+        if (i < i1 && j < k) acc[r] = fma(Q1[i * ldq + j], hv[u], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < SR_ROWS; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+#pragma unroll
+    for (int r = 0; r < SR_ROWS; ++r) {
+      const int64_t i = base + r;
+      if (i < i1) {
+        const T zi = zz[r] - acc[r];
+        if (lane == 0) {
+          z[i] = zi;
+          nacc = fma(zi, zi, nacc);
+        }
+      }
     }
   }
   nacc = block_sum(nacc, red);

@@ -165,7 +165,12 @@ int launch_gemm(cudaStream_t st, const ffsrqr_plan_s *P, unsigned char *ws, int 
   const int BM = small ? 32 : 64, BN = small ? 32 : (wide ? 128 : 64);
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   int splits = 1;
-  if (tiles < 2 * P->num_sms && K >= 512) {
+  if (small && K >= 128 && K < 512) {
+    // a k x k product: four K slices, so that four times the blocks run
+    // (each a quarter of the dependent loads) and one reduction adds them
+    splits = (int)std::min<int64_t>(4, (int64_t)P->part_cap / ((int64_t)M * N));
+    if (splits < 1) splits = 1;
+  } else if (tiles < 2 * P->num_sms && K >= 512) {
     splits = (int)cdiv(2 * P->num_sms, tiles);
     splits = (int)std::min<int64_t>(splits, K / 256);
     const int64_t cap = (int64_t)P->part_cap / ((int64_t)M * N);
