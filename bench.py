@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=24)
+    ap.add_argument("--block", type=int, default=0,
+                    help="TRQRCP block size b < k (Alg. 2; the sketch has b + p rows); 0: one block")
+    ap.add_argument("--g2-rows", type=int, default=0,
+                    help="SRQR test: 0 exact g2, d >= 1 Alg. 4's d-row random estimate")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the FP64 oracle run (cpu_baseline and the modes' errors against it)")
     ap.add_argument("--no-modes", action="store_true", help="skip the comparison of the three modes")
@@ -237,8 +241,13 @@ def config(a):
     gb = a.m * a.n * 4 / 1e9
     l2 = (f"inputs larger than L2 (A is {gb:.2f} GB), no flush" if gb > 0.129
           else f"A ({gb * 1e3:.0f} MB) fits in L2; steps run back to back without a flush")
-    return {"workload": workload_name(a), "m": a.m, "n": a.n, "k": a.k, "p": a.p,
-            "mode": a.mode, "l2": l2, "parallelism": f"replicas x{a.gpus}"}
+    cfg = {"workload": workload_name(a), "m": a.m, "n": a.n, "k": a.k, "p": a.p,
+           "mode": a.mode, "l2": l2, "parallelism": f"replicas x{a.gpus}"}
+    if getattr(a, "g2_rows", 0):
+        cfg["g2"] = f"d-row estimate, d = {a.g2_rows}"
+    if getattr(a, "block", 0):
+        cfg["block"] = a.block
+    return cfg
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -269,7 +278,8 @@ def run_ours(a, rank, world, local_rank):
     mode = {"mixed": ffsrqr.MIXED_TF32X3, "bf16x3": ffsrqr.MIXED_BF16X3, "plain": ffsrqr.PLAIN_FP32}[a.mode]
     r = min(2000, a.m, a.n)
     A = synth.decayed_torch(a.m, a.n, spectrum(a, r), 1e-6, seed=replica_seed(rank), device=str(dev))
-    plan = ffsrqr.Plan(a.m, a.n, a.k, a.p, mode, flags=ffsrqr.FLAG_PHASE_TIMES, device=dev)
+    plan = ffsrqr.Plan(a.m, a.n, a.k, a.p, mode, flags=ffsrqr.FLAG_PHASE_TIMES, device=dev,
+                       g2_rows=a.g2_rows, b=(a.block or None))
     out = plan.outputs()
     st = torch.cuda.current_stream(dev)
     for _ in range(a.warmup):

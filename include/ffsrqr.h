@@ -129,6 +129,24 @@ int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p,
 int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t l, int32_t p, int32_t mode,
                   const ffsrqr_opts_t *opts, size_t *workspace_bytes);
 
+/* The same with TRQRCP's block size b (Alg. 2) as an argument: the sketch has
+ * b + p rows, and the k pivots are chosen block by block.  For the block at
+ * positions jb..jb+bb-1 (bb = min(b, k - jb)): partial QRCP (Alg. 1) for bb
+ * steps on the current sample, the columns selected earlier excluded; the
+ * block's columns of A, orthogonalised against the earlier blocks' Q1 and
+ * factored ("QR on A(j:m, j:j+b-1)"); one pass over A for that block's rows
+ * of R = Q1^T A Pi; and, except after the last block, the sample update
+ * ("Update B(:, j+b:n)") B <- B - B(:, J) R_JJ^{-1} R(J, :), which keeps the
+ * sample equal to Omega (I - Q1 Q1^T) A.  The SRQR test, the swap loop and
+ * the rest of Alg. 9 are as in ffsrqr_plan (whose case is b = k); A is read
+ * 1 + ceil(k / b) + 1 times instead of three.  Requirements: those of
+ * ffsrqr_plan with b + p in place of k + p, 1 <= b <= k, and b a multiple of
+ * 8 when b < k (each block's first column keeps 32-byte row alignment).
+ * Errors: -1 plan NULL, -2 m, -3 n, -4 k, -5 b, -6 p, -7 mode, -8 opts, -9
+ * workspace_bytes NULL, and the statuses of ffsrqr_plan. */
+int ffsrqr_plan_blocked(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t b, int32_t p, int32_t mode,
+                        const ffsrqr_opts_t *opts, size_t *workspace_bytes);
+
 /* A plan that ffsrqr_run executes as approximate SVD by randomized subspace
  * iteration (the paper's appendix algorithm, the method Sec. 3.2 compares
  * against) with l = k + p columns and q iterations, on the same kernels:
@@ -173,6 +191,24 @@ const char *ffsrqr_status_string(int code);
 
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char *ffsrqr_last_cuda_error(void);
+
+/* The strong rank-revealing test's g2 = |alpha| ||Rtilde^{-T}||_{1,2} (Alg. 4,
+ * Rtilde = [[R11, a], [0, alpha]] of order l + 1): d = 0 (the default)
+ * computes it exactly; 1 <= d <= 32 uses Alg. 4's random estimate
+ * |alpha| / sqrt(d) ||Omega_t Rtilde^{-T}||_{1,2}, with Omega_t in
+ * N(0,1)^{d x (l+1)} drawn afresh for every test t of a run (t = 0 for the
+ * first test, t = s after the s-th swap): element (r, j) of Omega_t is element
+ * (t d + r)(l + 1) + j of Philox stream 1 under the run's seed (the stream
+ * definition of Omega, stream 0, with counter word 2 = 1).  The swap of
+ * Alg. 4 takes the argmax of the estimated column norms.  Column l + 1 of
+ * Rtilde^{-T} is e_{l+1} / alpha, whose term is exactly 1; the estimate is
+ * taken over columns 1..l and floored at 1 like the exact value.  The
+ * estimate costs d triangular solves with R11 instead of R11^{-1}.  Applies
+ * to the later runs of the plan; not for randomized-subspace-iteration plans.
+ * Errors: -1 plan NULL, -2 d outside [0, 32]; FFSRQR_STATUS_UNSUPPORTED for
+ * an RSISVD plan or when the swap kernel's shared memory does not fit;
+ * FFSRQR_STATUS_CUDA if the device query fails. */
+int ffsrqr_plan_set_g2_rows(ffsrqr_plan_t plan, int32_t d);
 
 /* Autotuner of the tensor-core launches (mixed modes): runs the pipeline on
  * the given problem (arguments as ffsrqr_run; outputs hold the last run)

@@ -90,11 +90,17 @@ def _load():
             lib.oracle_house_qr.argtypes = [P, i64, i64, i64, P, P]
             lib.oracle_srqr.argtypes = [P, i64, i64, i64, P, i64, i32, D, i32, P, P, P, P, P, P]
             lib.oracle_srqr.restype = ctypes.c_int
+            lib.oracle_srqr_x.argtypes = [P, i64, i64, i64, P, i64, i32, i32, D, i32, i32, u64,
+                                          P, P, P, P, P, P]
+            lib.oracle_srqr_x.restype = ctypes.c_int
             lib.oracle_jacobi_svd.argtypes = [P, i64, P, P, P]
             lib.oracle_jacobi_svd.restype = ctypes.c_int
             lib.oracle_ffsrqr.argtypes = [P, i64, i64, i64, i32, i32, u64, D, i32,
                                           P, P, P, P, P, P]
             lib.oracle_ffsrqr.restype = ctypes.c_int
+            lib.oracle_ffsrqr_x.argtypes = [P, i64, i64, i64, i32, i32, i32, u64, D, i32, i32,
+                                            P, P, P, P, P, P]
+            lib.oracle_ffsrqr_x.restype = ctypes.c_int
             lib.oracle_residual_fro.argtypes = [P, i64, i64, i64, P, P, P, i32]
             lib.oracle_residual_fro.restype = D
             _lib = lib
@@ -161,7 +167,12 @@ class SrqrResult:
     alpha_first: float
 
 
-def srqr(A, B, k: int, g: float = 2.0, max_swaps: int | None = None) -> SrqrResult:
+def srqr(A, B, k: int, g: float = 2.0, max_swaps: int | None = None, g2_rows: int = 0,
+         seed: int = 0, b: int | None = None) -> SrqrResult:
+    """Alg. 4 initialised by TRQRCP with block size b (None: b = k, one block;
+    B then has b + p rows).  g2_rows = d >= 1 replaces the exact g2 by Alg. 4's
+    d-row random estimate, its Omega_t drawn from Philox stream 1 under
+    `seed`."""
     A = _f64(A)
     B = _f64(B)
     m, n = A.shape
@@ -174,8 +185,9 @@ def srqr(A, B, k: int, g: float = 2.0, max_swaps: int | None = None) -> SrqrResu
     R = np.zeros((k, n))
     r0 = np.zeros(n)
     info = _SrqrInfo()
-    _load().oracle_srqr(_ptr(A), m, n, n, _ptr(B), s, k, g, max_swaps, _ptr(perm), _ptr(Q1),
-                        _ptr(R), _ptr(perm0), _ptr(r0), ctypes.byref(info))
+    _load().oracle_srqr_x(_ptr(A), m, n, n, _ptr(B), s, k, k if b is None else b, g, max_swaps,
+                          g2_rows, seed, _ptr(perm), _ptr(Q1), _ptr(R), _ptr(perm0), _ptr(r0),
+                          ctypes.byref(info))
     return SrqrResult(perm, Q1, R, perm0, r0, info.status, info.swaps, info.g2_first,
                       info.g2_final, info.cand_first, info.alpha_first)
 
@@ -208,18 +220,23 @@ class FfsrqrResult:
 
 
 def ffsrqr(A, k: int, p: int, seed: int = 0, g: float = 2.0, max_swaps: int | None = None,
-           trace: bool = False, l: int | None = None) -> FfsrqrResult:
+           trace: bool = False, l: int | None = None, g2_rows: int = 0,
+           b: int | None = None) -> FfsrqrResult:
     """Alg. 9 in FP64 on A (any float array, upcast to float64).  l (>= k) is
     the SRQR depth: SRQR and the SVD of A Pi Qhat_1 run at depth l, and the
-    leading k singular triplets are returned (Alg. 9's U_k, Sigma_k, V_k)."""
+    leading k singular triplets are returned (Alg. 9's U_k, Sigma_k, V_k).
+    g2_rows = d >= 1 uses Alg. 4's d-row random g2 estimate instead of the
+    exact g2.  b (< the depth) is TRQRCP's block size (Alg. 2): the sketch has
+    b + p rows and the pivots are chosen block by block; None: one block."""
     if l is not None and l != k:
         assert l > k
-        r = ffsrqr(A, l, p, seed, g, max_swaps, trace)
+        r = ffsrqr(A, l, p, seed, g, max_swaps, trace, g2_rows=g2_rows, b=b)
         r.U, r.S, r.V = r.U[:, :k].copy(), r.S[:k].copy(), r.V[:, :k].copy()
         return r
     A = _f64(A)
     m, n = A.shape
-    s = k + p
+    bs = k if b is None else b
+    s = bs + p
     if max_swaps is None:
         max_swaps = 4 * k
     U = np.zeros((m, k))
@@ -234,8 +251,8 @@ def ffsrqr(A, k: int, p: int, seed: int = 0, g: float = 2.0, max_swaps: int | No
               "Q1": np.zeros((m, k)), "R": np.zeros((k, n)), "Vp": np.zeros((n, k)),
               "Rhat": np.zeros((k, k)), "tmp": np.zeros((m, k))}
         tstruct = _Trace(*(_ptr(tr[f]) for f, _ in _Trace._fields_))
-    st = _load().oracle_ffsrqr(_ptr(A), m, n, n, k, p, seed, g, max_swaps, _ptr(U), _ptr(S),
-                               _ptr(V), _ptr(piv), ctypes.byref(info),
+    st = _load().oracle_ffsrqr_x(_ptr(A), m, n, n, k, bs, p, seed, g, max_swaps, g2_rows, _ptr(U),
+                                 _ptr(S), _ptr(V), _ptr(piv), ctypes.byref(info),
                                ctypes.byref(tstruct) if tstruct is not None else None)
     if st < 0:
         raise ValueError(f"oracle_ffsrqr rejected its arguments (code {st})")

@@ -13,16 +13,25 @@
  * Every routine follows the paper's algorithm steps in the paper's order, with
  * no blocking, fusion or reordering beyond plain loop order:
  *   Alg. 1  (partial QRCP)                      -> oracle_qrcp
- *   Alg. 2  (TRQRCP, block size b = k)          -> oracle_srqr, first half
- *   Alg. 4  (SRQR test and swap loop)           -> oracle_srqr, second half
- *   Alg. 9  (Flip-Flop SRQR)                    -> oracle_ffsrqr
+ *   Alg. 2  (TRQRCP, one block b = k, or b < k) -> oracle_srqr_x, first half
+ *   Alg. 4  (SRQR test and swap loop)           -> oracle_srqr_x, second half
+ *   Alg. 9  (Flip-Flop SRQR)                    -> oracle_ffsrqr_x
  * Readings of points the paper leaves open:
- *   - one TRQRCP block (b = k), SRQR depth l = k;
+ *   - one TRQRCP block (b = k) by default, SRQR depth l = k; with b < k
+ *     (blocked_pivots) the sketch has b + p rows and each block's pivots come
+ *     from QRCP on the sample updated by the earlier blocks;
  *   - the trailing-norm estimate of Alg. 4 uses the updated sample
  *     B2 - B1 R11^{-1} R12 (the sample of A(l+1:m, l+1:n) that TRQRCP's
  *     "update B" step produces), divided by b + p;
  *   - g2 = |alpha| * ||Rtilde^{-T}||_{1,2} is computed exactly (closed form)
- *     instead of through the d-row random estimator;
+ *     by default; with d >= 1 (oracle_srqr_x, oracle_ffsrqr_x) it is Alg. 4's
+ *     d-row random estimate |alpha|/sqrt(d) * ||Omega_t Rtilde^{-T}||_{1,2},
+ *     Omega_t in N(0,1)^{d x (l+1)} drawn afresh for every test t (0 for the
+ *     first, s after the s-th swap) from Philox stream 1: element (i, j) is
+ *     stream element (t d + i)(l+1) + j.  Column l+1 of Rtilde^{-T} is
+ *     e_{l+1}/alpha, so its term is exactly 1 and is not estimated; only
+ *     columns 1..l are, and the estimate is max(1, max_{i<=l} ...) like the
+ *     exact value;
  *   - every argmax breaks ties toward the lowest ORIGINAL column index;
  *   - "Round Robin rotation" = cyclic shift that moves the leaving column to
  *     position l+1, followed by Givens re-triangularisation;
@@ -390,24 +399,196 @@ static double g2_exact(const srqr_state *S, double alpha, int64_t *imax, int *si
     return g2;
 }
 
+/* Alg. 4's d-row estimate of g2 for test t: form Rtilde = [[R11, a],
+ * [0, alpha]] ((k+1) x (k+1), a = R(0:k, k) of the candidate), draw Omega_t
+ * (d x (k+1), Philox stream 1), solve Rtilde Y^T = Omega_t^T one row of
+ * Omega_t at a time (Y = Omega_t Rtilde^{-T}), and take
+ * |alpha|/sqrt(d) * (2-norm of column i of Y) for i < k; column k's term is
+ * exactly 1 (see the header).  alpha = 0 makes Rtilde singular: the
+ * estimate's limit |alpha| Y(:, i) -> -(R11^{-1} a)_i Omega_t(:, k) is used. */
+static double g2_estimate(const srqr_state *S, double alpha, int32_t d, uint64_t seed, int64_t t,
+                          int64_t *imax, int *singular)
+{
+    const int64_t n = S->n, k = S->k, kp = k + 1;
+    *singular = 0;
+    for (int64_t i = 0; i < k; ++i)
+        if (S->Rx[i * n + i] == 0.0) *singular = 1;
+    double g2 = 1.0;
+    *imax = -1;
+    if (*singular) return g2;
+    double *Rt = (double *)calloc((size_t)(kp * kp), sizeof(double));
+    for (int64_t i = 0; i < k; ++i)
+        for (int64_t j = i; j < kp; ++j) Rt[i * kp + j] = S->Rx[i * n + j];
+    Rt[k * kp + k] = alpha;
+    double *colsq = (double *)calloc((size_t)kp, sizeof(double));
+    double *y = (double *)malloc(sizeof(double) * (size_t)kp);
+    for (int64_t r = 0; r < d; ++r) {
+        for (int64_t j = 0; j < kp; ++j)
+            y[j] = oracle_normal(seed, 1u, (uint64_t)((t * d + r) * kp + j));
+        if (alpha != 0.0) {
+            upper_solve(Rt, kp, kp, y); /* y = Rtilde^{-1} omega_r^T, row r of Y */
+            for (int64_t i = 0; i < k; ++i) colsq[i] += (alpha * y[i]) * (alpha * y[i]);
+        } else {
+            const double wk = y[k];
+            for (int64_t i = 0; i < k; ++i) y[i] = S->Rx[i * n + k];
+            upper_solve(S->Rx, n, k, y);
+            for (int64_t i = 0; i < k; ++i) colsq[i] += (y[i] * wk) * (y[i] * wk);
+        }
+    }
+    for (int64_t i = 0; i < k; ++i) {
+        const double v = sqrt(colsq[i] / (double)d);
+        if (v > g2) {
+            g2 = v;
+            *imax = i;
+        }
+    }
+    free(Rt);
+    free(colsq);
+    free(y);
+    return g2;
+}
+
+static double g2_test(const srqr_state *S, double alpha, int32_t d, uint64_t seed, int64_t t,
+                      int64_t *imax, int *singular)
+{
+    return (d > 0) ? g2_estimate(S, alpha, d, seed, t, imax, singular)
+                   : g2_exact(S, alpha, imax, singular);
+}
+
+/* Alg. 2 (TRQRCP) with block size b < k: the pivots of the block starting at
+ * position jb come from bb = min(b, k - jb) steps of partial QRCP (Alg. 1) on
+ * the current sample, restricted to the columns not selected yet; the block's
+ * columns of A are then orthogonalised against the earlier blocks' Q
+ * (projected twice) and factored by Householder QR without pivoting ("QR on
+ * A(j:m, j:j+b-1)"), G_j = Q_j^T A is formed (one pass over A per block), and
+ * the sample is updated ("Update B(:, j+b:n)"):
+ *   B <- B - B(:, J_j) R_jj^{-1} G_j,   R_jj = upper triangle of G_j(:, J_j),
+ * which keeps B = Omega (I - Q Q^T) A, the sample of the trailing matrix.
+ * perm[0:k] receives the pivots in order, perm[k:n] the other columns in
+ * ascending order.  The QR factors themselves are recomputed by the caller
+ * (the QR of A(:, perm[0:k]) with a positive diagonal is unique, and block
+ * Gram-Schmidt with positive diagonals produces the same factors). */
+static int blocked_pivots(const double *A, int64_t m, int64_t n, int64_t lda, const double *B0,
+                          int64_t s, int32_t k, int32_t b, int32_t *perm)
+{
+    int status = ORACLE_OK;
+    double *B = (double *)malloc(sizeof(double) * (size_t)(s * n));
+    memcpy(B, B0, sizeof(double) * (size_t)(s * n));
+    int *sel = (int *)calloc((size_t)n, sizeof(int));
+    double *Q = (double *)calloc((size_t)(m * k), sizeof(double));
+    double *Bc = (double *)malloc(sizeof(double) * (size_t)(s * n));
+    int32_t *map = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *pc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *G = (double *)malloc(sizeof(double) * (size_t)(b * n));
+    double *Qt = (double *)malloc(sizeof(double) * (size_t)(b * m));
+    double *h = (double *)malloc(sizeof(double) * (size_t)k);
+    double *x = (double *)malloc(sizeof(double) * (size_t)b);
+    for (int32_t jb = 0; jb < k; jb += b) {
+        const int32_t bb = (k - jb < b) ? k - jb : b;
+        /* partial QRCP on the unselected columns (ascending original order) */
+        int64_t nu = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (!sel[i]) map[nu++] = (int32_t)i;
+        for (int64_t t = 0; t < s; ++t)
+            for (int64_t c = 0; c < nu; ++c) Bc[t * nu + c] = B[t * n + map[c]];
+        if (oracle_qrcp(Bc, s, nu, bb, pc) != ORACLE_OK) status = ORACLE_RANK_DEFICIENT;
+        for (int32_t t = 0; t < bb; ++t) {
+            perm[jb + t] = map[pc[t]];
+            sel[map[pc[t]]] = 1;
+        }
+        /* the block's columns, projected twice against Q(:, 0:jb), then QR */
+        double *Y = (double *)malloc(sizeof(double) * (size_t)(m * bb));
+        double *Qj = (double *)malloc(sizeof(double) * (size_t)(m * bb));
+        double *Rj = (double *)malloc(sizeof(double) * (size_t)(bb * bb));
+        for (int64_t t = 0; t < m; ++t)
+            for (int32_t c = 0; c < bb; ++c) Y[t * bb + c] = A[t * lda + perm[jb + c]];
+        for (int pass = 0; pass < 2 && jb > 0; ++pass) {
+            for (int32_t c = 0; c < bb; ++c) {
+                for (int32_t i = 0; i < jb; ++i) {
+                    double v = 0.0;
+                    for (int64_t t = 0; t < m; ++t) v += Q[t * k + i] * Y[t * bb + c];
+                    h[i] = v;
+                }
+                for (int64_t t = 0; t < m; ++t) {
+                    double v = Y[t * bb + c];
+                    for (int32_t i = 0; i < jb; ++i) v -= Q[t * k + i] * h[i];
+                    Y[t * bb + c] = v;
+                }
+            }
+        }
+        oracle_house_qr(Y, m, bb, bb, Qj, Rj);
+        for (int64_t t = 0; t < m; ++t)
+            for (int32_t c = 0; c < bb; ++c) Q[t * k + jb + c] = Qj[t * bb + c];
+        if (jb + bb < k) {
+            /* G_j = Q_j^T A (bb x n) */
+            for (int64_t t = 0; t < m; ++t)
+                for (int32_t c = 0; c < bb; ++c) Qt[c * m + t] = Qj[t * bb + c];
+            mat_mul(Qt, A, lda, G, bb, m, n);
+            /* B <- B - B(:, J_j) R_jj^{-1} G_j, column by column, from the
+             * block's columns before the update */
+            double *BJ = (double *)malloc(sizeof(double) * (size_t)(s * bb));
+            for (int64_t t = 0; t < s; ++t)
+                for (int32_t c = 0; c < bb; ++c) BJ[t * bb + c] = B[t * n + perm[jb + c]];
+            for (int64_t i = 0; i < n; ++i) {
+                for (int32_t c = 0; c < bb; ++c) x[c] = G[c * n + i];
+                for (int32_t r = bb - 1; r >= 0; --r) { /* x = R_jj^{-1} G_j(:, i) */
+                    double v = x[r];
+                    for (int32_t c = r + 1; c < bb; ++c) v -= G[r * n + perm[jb + c]] * x[c];
+                    x[r] = v / G[r * n + perm[jb + r]];
+                }
+                for (int64_t t = 0; t < s; ++t) {
+                    double v = 0.0;
+                    for (int32_t c = 0; c < bb; ++c) v += BJ[t * bb + c] * x[c];
+                    B[t * n + i] -= v;
+                }
+            }
+            free(BJ);
+        }
+        free(Y);
+        free(Qj);
+        free(Rj);
+    }
+    int64_t pos = k;
+    for (int64_t i = 0; i < n; ++i)
+        if (!sel[i]) perm[pos++] = (int32_t)i;
+    free(B);
+    free(sel);
+    free(Q);
+    free(Bc);
+    free(map);
+    free(pc);
+    free(G);
+    free(Qt);
+    free(h);
+    free(x);
+    return status;
+}
+
 /* Run SRQR (Alg. 4, initialised by TRQRCP with b = k, Alg. 2) to depth l = k.
  * Inputs: A (m x n, lda), the sketch B = Omega A (s x n).
  * Outputs: perm (n), Q1 (m x k), R (k x n, pivot order), initial QRCP pivots
  * perm0 (n, may be NULL), trailing estimates r0 (n, pivot order of perm0 after
  * the candidate swap, may be NULL). */
-int oracle_srqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *B, int64_t s,
-                int32_t k, double g, int32_t max_swaps, int32_t *perm, double *Q1, double *R,
-                int32_t *perm0, double *r0, oracle_srqr_info *info)
+int oracle_srqr_x(const double *A, int64_t m, int64_t n, int64_t lda, const double *B, int64_t s,
+                  int32_t k, int32_t b, double g, int32_t max_swaps, int32_t d, uint64_t seed,
+                  int32_t *perm, double *Q1, double *R, int32_t *perm0, double *r0,
+                  oracle_srqr_info *info)
 {
     const int64_t kp = k + 1;
     oracle_srqr_info inf;
     memset(&inf, 0, sizeof inf);
     inf.cand_first = -1;
-    /* Alg. 2: partial QRCP on B to obtain the k pivots */
-    double *Bw = (double *)malloc(sizeof(double) * (size_t)(s * n));
-    memcpy(Bw, B, sizeof(double) * (size_t)(s * n));
-    int status = oracle_qrcp(Bw, s, n, k, perm);
-    free(Bw);
+    /* Alg. 2: partial QRCP on B to obtain the k pivots (one block, b >= k),
+     * or the blocked TRQRCP selection */
+    int status;
+    if (b >= k) {
+        double *Bw = (double *)malloc(sizeof(double) * (size_t)(s * n));
+        memcpy(Bw, B, sizeof(double) * (size_t)(s * n));
+        status = oracle_qrcp(Bw, s, n, k, perm);
+        free(Bw);
+    } else {
+        status = blocked_pivots(A, m, n, lda, B, s, k, b, perm);
+    }
     if (perm0) memcpy(perm0, perm, sizeof(int32_t) * (size_t)n);
 
     /* Alg. 2: QR (no pivoting) of the pivoted panel A(:, perm[0:k]) */
@@ -475,7 +656,7 @@ int oracle_srqr(const double *A, int64_t m, int64_t n, int64_t lda, const double
         inf.alpha_first = alpha;
         int64_t imax;
         int sing2;
-        double g2 = g2_exact(&S, alpha, &imax, &sing2);
+        double g2 = g2_test(&S, alpha, d, seed, 0, &imax, &sing2);
         inf.g2_first = g2;
         int32_t swaps = 0;
         while (g2 > g && swaps < max_swaps) {
@@ -520,8 +701,8 @@ int oracle_srqr(const double *A, int64_t m, int64_t n, int64_t lda, const double
             c = argmax_trailing(&S, k);
             swap_cols(&S, k, c, k);
             alpha = one_step_qr(&S);
-            g2 = g2_exact(&S, alpha, &imax, &sing2);
             ++swaps;
+            g2 = g2_test(&S, alpha, d, seed, swaps, &imax, &sing2);
         }
         inf.swaps = swaps;
         inf.g2_final = g2;
@@ -541,6 +722,14 @@ int oracle_srqr(const double *A, int64_t m, int64_t n, int64_t lda, const double
     inf.status = status;
     if (info) *info = inf;
     return status;
+}
+
+/* oracle_srqr_x with one TRQRCP block (b = k) and the exact g2 (d = 0). */
+int oracle_srqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *B, int64_t s,
+                int32_t k, double g, int32_t max_swaps, int32_t *perm, double *Q1, double *R,
+                int32_t *perm0, double *r0, oracle_srqr_info *info)
+{
+    return oracle_srqr_x(A, m, n, lda, B, s, k, k, g, max_swaps, 0, 0, perm, Q1, R, perm0, r0, info);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -652,12 +841,16 @@ static void sign_rule(double *U, double *V, int64_t m, int64_t n, int64_t k)
     }
 }
 
-int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k, int32_t p,
-                  uint64_t seed, double g, int32_t max_swaps, double *U, double *S, double *V,
-                  int32_t *piv, oracle_info *info, oracle_trace *trace)
+/* Alg. 9 with TRQRCP block size b (1 <= b <= k; the sketch has b + p rows)
+ * and g2 exact (d = 0) or Alg. 4's d-row estimate (d >= 1, Omega_t from the
+ * run's seed). */
+int oracle_ffsrqr_x(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k, int32_t b,
+                    int32_t p, uint64_t seed, double g, int32_t max_swaps, int32_t d, double *U,
+                    double *S, double *V, int32_t *piv, oracle_info *info, oracle_trace *trace)
 {
-    if (k < 1 || k > n || k > m || p < 0 || (int64_t)k + p > m || lda < n) return -1;
-    const int64_t s = (int64_t)k + p;
+    if (d < 0 || b < 1 || b > k) return -1;
+    if (k < 1 || k > n || k > m || p < 0 || (int64_t)b + p > m || lda < n) return -1;
+    const int64_t s = (int64_t)b + p;
     oracle_info inf;
     memset(&inf, 0, sizeof inf);
 
@@ -673,8 +866,8 @@ int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k,
     double *Q1 = (double *)malloc(sizeof(double) * (size_t)(m * k));
     double *R = (double *)malloc(sizeof(double) * (size_t)(k * n));
     oracle_srqr_info si;
-    oracle_srqr(A, m, n, lda, B, s, k, g, max_swaps, piv, Q1, R, trace ? trace->perm0 : NULL,
-                trace ? trace->r0 : NULL, &si);
+    oracle_srqr_x(A, m, n, lda, B, s, k, b, g, max_swaps, d, seed, piv, Q1, R,
+                  trace ? trace->perm0 : NULL, trace ? trace->r0 : NULL, &si);
     free(B);
     inf.status = si.status;
     inf.swaps = si.swaps;
@@ -735,6 +928,13 @@ int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k,
     sign_rule(U, V, m, n, k);
     if (info) *info = inf;
     return inf.status;
+}
+
+int oracle_ffsrqr(const double *A, int64_t m, int64_t n, int64_t lda, int32_t k, int32_t p,
+                  uint64_t seed, double g, int32_t max_swaps, double *U, double *S, double *V,
+                  int32_t *piv, oracle_info *info, oracle_trace *trace)
+{
+    return oracle_ffsrqr_x(A, m, n, lda, k, k, p, seed, g, max_swaps, 0, U, S, V, piv, info, trace);
 }
 
 /* Frobenius residual ||A - U diag(S) V^T||_F, accumulated in FP64 without

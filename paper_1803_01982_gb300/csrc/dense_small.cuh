@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace ffq {
 
@@ -765,6 +766,154 @@ __global__ void srqr_g2_kernel(const T *__restrict__ npart, int nnp, const T *__
     }
     ctl[CTL_IMAX] = (bi == 0x7fffffff) ? -1 : bi;
     const int need = (g2 > g) ? 1 : 0;
+    ctl[CTL_NEED_SWAP] = (need && ctl[CTL_SWAPS] < max_swaps) ? 1 : 0;
+    if (need && ctl[CTL_SWAPS] >= max_swaps) set_status(ctl, STATUS_SWAP_CAP);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 4's d-row random estimate of g2 = |alpha| ||Rtilde^{-T}||_{1,2}:
+//   g2 ~ |alpha| / sqrt(d) ||Omega_t Rtilde^{-T}||_{1,2},
+// Omega_t in N(0,1)^{d x (k+1)} drawn afresh for test t (0: the first test,
+// s: the test after the s-th swap); element (r, j) is element (t d + r)(k+1) + j
+// of Philox stream G2EST_STREAM under the run's seed.  Column r of
+// |alpha| Rtilde^{-1} Omega_t^T is, with Rtilde = [[R11, a], [0, alpha]] and
+// alpha >= 0, [R11^{-1} (alpha w_top - a w_k); w_k] (w = row r of Omega_t),
+// so one back substitution with R11 per row of Omega_t gives it, also at
+// alpha = 0.  The candidate's own column of Rtilde^{-T} is e_{k+1} / alpha,
+// whose term is exactly 1; only columns 0..k-1 are estimated, and the
+// estimate is max(1, max_i sqrt(sum_r y_r(i)^2 / d)) like the exact form.
+// ---------------------------------------------------------------------------
+constexpr uint32_t G2EST_STREAM = 1;
+constexpr int G2EST_MAX_D = 32;
+constexpr int G2EST_YU = 8;  // rows per lane: k <= 256
+
+// Shared memory (elements of T) of g2est_block for depth k.
+__host__ __device__ inline int g2est_smem_elems(int k) { return ((k + 31) / 32) * 32 * 33 + k; }
+
+// One block: colsq[i] = sum_r y_r(i)^2 for i < k (rows r in increasing order).
+// R11 (k x k, upper, row-major, leading dimension ldr), a (k) and alpha as
+// above.  The block's warps take the rows of Omega_t in rounds; R11 is staged
+// through shared memory 32 columns at a time (padded to 33) for all warps.
+// Returns nonzero (in every thread) if R11 has a zero diagonal entry.
+template <typename T>
+__device__ int g2est_block(const T *__restrict__ R11, int64_t ldr, const T *a, T alpha, int k, int d,
+                           uint64_t seed, int64_t t, T *smem) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int nchunk = (k + 31) / 32;
+  T *chunk = smem;                    // (32 nchunk) x 33
+  T *colsq = smem + nchunk * 32 * 33;  // k
+  __shared__ int s_zero;
+  if (threadIdx.x == 0) s_zero = 0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) colsq[i] = T(0);
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (R11[(int64_t)i * ldr + i] == T(0)) s_zero = 1;
+  for (int r0 = 0; r0 < d; r0 += nwarp) {
+    const int r = r0 + wid;
+    const bool solver = r < d;
+    const uint64_t e0 = (uint64_t)((t * d + r) * (int64_t)(k + 1));
+    T y[G2EST_YU];
+    const T wk = solver ? gauss_elem<T>(seed, G2EST_STREAM, e0 + (uint64_t)k) : T(0);
+#pragma unroll
+    for (int u = 0; u < G2EST_YU; ++u) {
+      const int row = lane + 32 * u;
+      y[u] = (solver && row < k) ? fma(alpha, gauss_elem<T>(seed, G2EST_STREAM, e0 + (uint64_t)row), -a[row] * wk)
+                                 : T(0);
+    }
+#pragma unroll
+    for (int ub = G2EST_YU - 1; ub >= 0; --ub) {
+      if (ub >= nchunk) continue;
+      const int i0 = ub * 32, rows = i0 + 32;
+      __syncthreads();  // the previous chunk is consumed
+      for (int e = threadIdx.x; e < rows * 32; e += blockDim.x) {
+        const int row = e >> 5, col = i0 + (e & 31);
+        chunk[row * 33 + (e & 31)] = (col < k && row <= col) ? R11[(int64_t)row * ldr + col] : T(0);
+      }
+      __syncthreads();
+      if (solver) {
+        const int top = min(31, k - 1 - i0);
+        for (int ii = top; ii >= 0; --ii) {
+          const T dg = chunk[(i0 + ii) * 33 + ii];
+          const T yv = __shfl_sync(0xffffffffu, y[ub], ii);
+          const T yi = (dg != T(0)) ? yv / dg : T(0);
+#pragma unroll
+          for (int u = 0; u < G2EST_YU; ++u) {
+            if (u > ub) continue;
+            const int row = lane + 32 * u;
+            if (row < i0 + ii) y[u] = fma(-chunk[row * 33 + ii], yi, y[u]);
+          }
+          if (lane == ii) y[ub] = yi;
+        }
+      }
+    }
+    // fixed-order accumulation over the rows of Omega_t
+    for (int w = 0; w < nwarp; ++w) {
+      if (w == wid && solver) {
+#pragma unroll
+        for (int u = 0; u < G2EST_YU; ++u) {
+          const int row = lane + 32 * u;
+          if (row < k) colsq[row] = fma(y[u], y[u], colsq[row]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  return s_zero;
+}
+
+// The first SRQR test with the d-row estimate (one block, 1024 threads,
+// dynamic shared memory g2est_smem_elems(k) elements): alpha from the
+// residual partial sums, R11 in position order, a = R(0:k, c) = Gt row c.
+template <typename T>
+__global__ void __launch_bounds__(1024) srqr_g2est_kernel(const T *__restrict__ npart, int nnp,
+                                                          const T *__restrict__ R11, int k,
+                                                          const T *__restrict__ Gt, int64_t ldg, int d,
+                                                          uint64_t seed, double g, int max_swaps, int *ctl,
+                                                          double *dctl) {
+  extern __shared__ __align__(16) unsigned char g2e_raw[];
+  T *sm = reinterpret_cast<T *>(g2e_raw);
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_alpha;
+  const int c = ctl[CTL_CAND];
+  if (c == 0x7fffffff) {
+    if (threadIdx.x == 0) {
+      dctl[D_G2] = 1.0;
+      dctl[D_G2_FIRST] = 1.0;
+      ctl[CTL_NEED_SWAP] = 0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    T acc = T(0);
+    for (int b = 0; b < nnp; ++b) acc += npart[b];
+    s_alpha = sqrt(acc);
+  }
+  __syncthreads();
+  const T alpha = s_alpha;
+  const int zero = g2est_block<T>(R11, k, Gt + (int64_t)c * ldg, alpha, k, d, seed, 0, sm);
+  const T *colsq = sm + ((k + 31) / 32) * 32 * 33;
+  T bv = T(1);
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const T val = sqrt(colsq[i] / T(d));
+    if (better(val, i, bv, bi)) {
+      bv = val;
+      bi = i;
+    }
+  }
+  block_argmax(bv, bi, red_v, red_i);
+  if (threadIdx.x == 0) {
+    const double g2 = zero ? 1.0 : (double)bv;
+    dctl[D_G2] = g2;
+    dctl[D_ALPHA] = (double)alpha;
+    dctl[D_G2_FIRST] = g2;
+    dctl[D_ALPHA_FIRST] = (double)alpha;
+    ctl[CTL_CAND_FIRST] = c;
+    ctl[CTL_IMAX] = (zero || bi == 0x7fffffff) ? -1 : bi;
+    const int need = (g2 > g && !zero && bi != 0x7fffffff) ? 1 : 0;
     ctl[CTL_NEED_SWAP] = (need && ctl[CTL_SWAPS] < max_swaps) ? 1 : 0;
     if (need && ctl[CTL_SWAPS] >= max_swaps) set_status(ctl, STATUS_SWAP_CAP);
   }

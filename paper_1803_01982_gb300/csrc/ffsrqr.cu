@@ -112,6 +112,8 @@ struct ffsrqr_plan_s {
   size_t off_rowk, off_qk, off_rot, off_rd, off_xinv, off_swpart, off_swbv, off_swbi;  // swap loop
   int swap_grid;
   size_t swap_smem;
+  int g2_rows = 0;  // 0: exact g2; d >= 1: Alg. 4's d-row random estimate
+  int blk = 0;      // TRQRCP block size b (Alg. 2); b = k: one block
   size_t part_cap;  // elements of the split-K buffer
   int qrcp_grid, qrcp_threads;
   int smem_optin;  // max dynamic shared memory per block (bytes)
@@ -144,6 +146,14 @@ struct ffsrqr_plan_s {
   } while (0)
 
 namespace {
+
+// Dynamic shared memory of srqr_swap_kernel: carry (k + 1), a, h (k each)
+// and the per-warp rows (16 k), which the d-row g2 estimate reuses for its
+// staged R11 columns and column sums.
+size_t swap_smem_bytes(int k, int g2_rows, size_t elem) {
+  const size_t tail = (size_t)(g2_rows > 0 ? std::max(16 * k, g2est_smem_elems(k)) : 16 * k);
+  return ((size_t)(3 * k + 1) + tail) * elem;
+}
 
 constexpr long long kSpinLimit = 2000000;  // ~1 s of polling (each poll is an L2 round trip + 20 ns sleep)
 // Largest ||X1^T X1 - I||_F for which the second Cholesky-QR sweep uses the
@@ -492,7 +502,7 @@ __global__ void info_kernel(const int *ctl, const double *dctl, ffsrqr_info_t *i
 // estimates, one-step QR residual alpha, closed-form g2.
 template <typename T>
 int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A, int64_t lda,
-              int first) {
+              uint64_t seed, int first) {
   const int k = P->k;
   srqr_pick_kernel<T><<<1, 256, 0, st>>>(w.bv, w.bi, P->nblk_tn, w.gt, P->ldk, k, w.avec, w.ctl);
   CKL("srqr_pick");
@@ -504,6 +514,12 @@ int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A,
   srqr_reorth_kernel<T><<<P->nblk_res, threads, (size_t)k * sizeof(T), st>>>(
       P->m, w.q1, P->ldk, k, w.hpart, P->nblk_res, w.ctl, w.z, w.npart);
   CKL("srqr_reorth");
+  if (P->g2_rows > 0) {
+    srqr_g2est_kernel<T><<<1, 1024, (size_t)g2est_smem_elems(k) * sizeof(T), st>>>(
+        w.npart, P->nblk_res, w.r11, k, w.gt, P->ldk, P->g2_rows, seed, P->g, P->max_swaps, w.ctl, w.dctl);
+    CKL("srqr_g2est");
+    return 0;
+  }
   srqr_g2_kernel<T><<<1, 256, 0, st>>>(w.npart, P->nblk_res, w.rinv, k, w.zt, P->ldk, P->g,
                                        P->max_swaps, w.ctl, w.dctl, first);
   CKL("srqr_g2");
@@ -715,6 +731,108 @@ cudaError_t launch_jacobi_blk(cudaStream_t st, const float *M, int kk, int ldm, 
 // item 8, and Q_t, V' in place).  The phase-batched runs of a batch or a
 // server run this part of several problems, their small SVDs in one launch,
 // then run_post.
+// Alg. 2 (TRQRCP) with block size b < k, replacing the one-block a3-a5.
+// The sketch B (b + p rows) is copied to a working sample (the trailing-norm
+// buffer, free until the SRQR test); for the block at positions jb..jb+bb-1:
+//   - partial QRCP for bb steps on the working sample, the columns selected
+//     by earlier blocks excluded (their marks in sel), pivots to piv[jb:];
+//   - Y = A(:, J_j), projected twice against Q1(:, 0:jb) (block classical
+//     Gram-Schmidt, the products on the CUDA cores), preconditioned by the
+//     sample's R factor S11 of the block and orthonormalised by CholeskyQR2
+//     into Q1(:, jb:jb+bb);
+//   - one pass over A: G^T(:, jb:jb+bb) = A^T Q_j (the rows of R = Q1^T A Pi
+//     that the one-block pipeline forms in its pass 2);
+//   - unless it is the last block, the sample update
+//     B <- B - B(:, J_j) R_jj^{-1} G_j   (R_jj the upper triangle of G_j(:, J_j)),
+//     so that the sample stays Omega (I - Q Q^T) A, the sample of the
+//     trailing matrix.
+// The block's factor products run through a copy of the plan with k = bb
+// (leading dimensions unchanged).  b is a multiple of 8 (plan check), so
+// every block's first column keeps 32-byte row alignment.
+template <typename T>
+int run_blocked(ffsrqr_plan_s *P, const T *A, int64_t lda, int32_t *piv, unsigned char *ws, WsPtrs<T> &w,
+                cudaStream_t st, bool tc) {
+  const int64_t m = P->m, n = P->n;
+  const int k = P->k, s = P->s, b = P->blk;
+  const int64_t lds = P->lds, ldk = P->ldk;
+  const int nsm = P->num_sms;
+  T *smp = w.cbt;
+  int rc;
+  CK(cudaMemcpyAsync(smp, w.bt, (size_t)n * lds * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  for (int jb = 0; jb < k; jb += b) {
+    const int bb = std::min(b, k - jb);
+    const bool last = jb + bb == k;
+    ffsrqr_plan_s Pb = *P;
+    Pb.k = bb;
+    if (jb > 0) {  // the QRCP kernel's barrier counter and winner keys start at zero
+      CK(cudaMemsetAsync(w.ctl + CTL_BARRIER0, 0, sizeof(int), st));
+      CK(cudaMemsetAsync(w.ctl + CTL_WIN_KEY, 0, 6 * sizeof(int), st));
+    }
+    QrcpArgs<T> qa;
+    qa.Bt = smp;
+    qa.n = n;
+    qa.s = s;
+    qa.lds = (int)lds;
+    qa.k = bb;
+    qa.piv = piv + jb;
+    qa.S11 = w.s11;
+    qa.cand_val = w.cval;
+    qa.cand_idx = w.cidx;
+    qa.cand_col = w.ccol;
+    qa.sel = w.sel;
+    qa.presel = w.sel;
+    qa.ctl = w.ctl;
+    qa.spin_limit = kSpinLimit;
+    qa.stall_step = (last && (P->flags & FFSRQR_FLAG_TEST_STALL)) ? bb - 1 : -1;
+    qa.cols_per_block = P->qrcp_cols;
+    qa.s_pad = P->qrcp_spad;
+    void *args[] = {&qa};
+    CK(smem_cap_max((const void *)qrcp_kernel<T>));
+    CK(cudaLaunchCooperativeKernel((void *)qrcp_kernel<T>, dim3(P->qrcp_grid), dim3(P->qrcp_threads), args,
+                                   P->qrcp_smem, st));
+    ++g_launches;
+    posdiag_rows_kernel<T><<<(unsigned)cdiv((int64_t)bb * 32, 256), 256, 0, st>>>(w.s11, bb);
+    CKL("posdiag");
+    T *Y = w.q1 + jb;
+    gather_cols_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(m * bb, 256), 8 * nsm), 256, 0, st>>>(
+        A, lda, m, bb, piv + jb, Y, ldk);
+    CKL("gather_cols");
+    for (int r = 0; r < 2 && jb > 0; ++r) {
+      // C (jb x bb) = Q1(:, 0:jb)^T Y, then Y -= Q1(:, 0:jb) C
+      if ((rc = launch_gemm<T>(st, P, ws, jb, bb, (int)m, w.q1, ldk, true, Y, ldk, true, w.rinv, bb))) return rc;
+      if ((rc = launch_gemm<T>(st, P, ws, (int)m, bb, jb, w.q1, ldk, false, w.rinv, bb, true, Y, ldk, T(-1),
+                               T(1))))
+        return rc;
+    }
+    if ((rc = launch_trsm<T, true>(st, &Pb, Y, ldk, m, w.s11, bb, 1))) return rc;
+    if (tc) {
+      if ((rc = cholqr2_tc(st, &Pb, ws, (const float *)Y, m, (float *)Y, nullptr))) return rc;
+      if ((rc = tc_thin_pass(st, &Pb, ws, true, (const float *)A, lda, (const float *)Y, m, (float *)(w.gt + jb))))
+        return rc;
+    } else {
+      if ((rc = cholqr2<T>(st, &Pb, ws, Y, ldk, m, nullptr))) return rc;
+      if ((rc = launch_gemm<T>(st, P, ws, (int)n, bb, (int)m, A, lda, true, Y, ldk, true, w.gt + jb, ldk)))
+        return rc;
+    }
+    if (last) break;
+    // sample update: B^T -= Z_j^T B(:, J_j)^T, Z_j^T = G_j^T R_jj^{-T}
+    extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)bb * bb, 256), 256, 0, st>>>(w.gt + jb, ldk, bb, piv + jb,
+                                                                                  w.r11, nullptr);
+    CKL("extract_r11");
+    copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * 32, 256), 8 * nsm), 256, 0, st>>>(w.gt + jb, ldk, w.zt,
+                                                                                           ldk, n, bb, nullptr);
+    CKL("copy_zt");
+    if ((rc = launch_trsm<T, false>(st, &Pb, w.zt, ldk, n, w.r11, 1, bb))) return rc;
+    gather_rows_kernel<T><<<(unsigned)cdiv((int64_t)bb * s, 256), 256, 0, st>>>(smp, lds, bb, s, piv + jb, w.bjt,
+                                                                                lds);
+    CKL("gather_rows");
+    if ((rc = launch_gemm<T>(st, P, ws, (int)n, s, bb, w.zt, ldk, false, w.bjt, lds, true, smp, lds, T(-1),
+                             T(1))))
+      return rc;
+  }
+  return 0;
+}
+
 template <typename T>
 int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *piv, unsigned char *ws,
             cudaStream_t st) {
@@ -766,6 +884,13 @@ int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *p
   }
   // a3: QRCP on the sketch
   MARK(2);
+  if (P->blk < k) {
+    // a3-a5 block by block (Alg. 2 with b < k); its phase times all fall
+    // under the QRCP mark
+    if ((rc = run_blocked<T>(P, A, lda, piv, ws, w, st, tc))) return rc;
+    MARK(3);
+    MARK(4);
+  } else {
   {
     QrcpArgs<T> qa;
     qa.Bt = w.bt;
@@ -811,13 +936,16 @@ int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *p
   } else if ((rc = launch_gemm<T>(st, P, ws, (int)n, k, (int)m, A, lda, true, w.q1, ldk, true, w.gt, ldk))) {
     return rc;
   }
+  }
   MARK(5);
   // a6: R11, R11^{-1}, Z^T = G^T R11^{-T}
   extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11, nullptr);
   CKL("extract_r11");
-  eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k, k);
-  CKL("eye");
-  if ((rc = launch_trsm<T, true>(st, P, w.rinv, k, k, w.r11, k, 1))) return rc;
+  if (P->g2_rows == 0) {  // R11^{-1} for the exact g2 (the estimate solves with R11 itself)
+    eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k, k);
+    CKL("eye");
+    if ((rc = launch_trsm<T, true>(st, P, w.rinv, k, k, w.r11, k, 1))) return rc;
+  }
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, w.zt,
                                                                                           ldk, n, k, nullptr);
   CKL("copy_zt");
@@ -836,7 +964,7 @@ int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *p
   trailing_norms_kernel<T><<<P->nblk_tn, 256, 0, st>>>(w.bt, w.cbt, lds, n, s, w.sel, w.r, w.bv, w.bi);
   CKL("trailing_norms");
   if (k < n) {
-    if ((rc = srqr_test<T>(st, P, w, A, lda, 1))) return rc;
+    if ((rc = srqr_test<T>(st, P, w, A, lda, seed, 1))) return rc;
   }
   MARK(6);
   // a7: swap loop (Alg. 4) while g2 > g, entirely on the device; afterwards
@@ -870,6 +998,8 @@ int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *p
     sa.g = P->g;
     sa.max_swaps = P->max_swaps;
     sa.spin_limit = kSpinLimit;
+    sa.g2_rows = P->g2_rows;
+    sa.seed = seed;
     void *args[] = {&sa};
     CK(smem_cap_max((const void *)srqr_swap_kernel<T>));
     CK(cudaLaunchCooperativeKernel((void *)srqr_swap_kernel<T>, dim3(P->swap_grid), dim3(512), args,
@@ -1303,6 +1433,21 @@ int plan_jacobi(ffsrqr_plan_s *P) {
   return P->jac_cluster ? 0 : FFSRQR_STATUS_UNSUPPORTED;
 }
 
+// Switch the SRQR test between the exact g2 (d = 0) and the d-row estimate,
+// resizing the swap kernel's shared memory for it.
+template <typename T>
+int plan_g2_rows(ffsrqr_plan_s *P, int d) {
+  const size_t bytes = swap_smem_bytes(P->k, d, sizeof(T));
+  if (bytes > (size_t)P->smem_optin) return FFSRQR_STATUS_UNSUPPORTED;
+  int per_sm = 0;
+  CK(smem_cap_max((const void *)srqr_swap_kernel<T>));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srqr_swap_kernel<T>, 512, bytes));
+  if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
+  P->swap_smem = bytes;
+  P->g2_rows = d;
+  return 0;
+}
+
 template <typename T>
 int plan_qrcp(ffsrqr_plan_s *P) {
   const int s = P->s;
@@ -1334,7 +1479,7 @@ int plan_qrcp(ffsrqr_plan_s *P) {
   if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
   P->qrcp_grid = (int)grid;
   // swap loop: one co-resident block of 512 threads per SM
-  P->swap_smem = (size_t)(P->k + 1 + 2 * P->k + 16 * P->k) * sizeof(T);
+  P->swap_smem = swap_smem_bytes(P->k, P->g2_rows, sizeof(T));
   CK(smem_cap_max((const void *)srqr_swap_kernel<T>));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srqr_swap_kernel<T>, 512, P->swap_smem));
   if (per_sm < 1) return FFSRQR_STATUS_UNSUPPORTED;
@@ -1342,35 +1487,10 @@ int plan_qrcp(ffsrqr_plan_s *P) {
   return 0;
 }
 
-}  // namespace
-
-extern "C" {
-
-int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
-                const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
-  return ffsrqr_plan_l(plan, m, n, k, k, p, mode, opts, workspace_bytes);
-}
-
-int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32_t k, int32_t p, int32_t mode,
-                  const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
-  // here k is Alg. 9's SRQR depth l and kout its target rank; the checks
-  // below use ffsrqr_plan's argument numbers, shifted by one after kout
-  if (!plan) return -1;
-  *plan = nullptr;
-  if (kout < 1 || kout > k) {
-    if (k >= 1 && kout > k) return -5;
-    return -4;
-  }
-  if (m < 1 || m > (int64_t)INT32_MAX) return -2;
-  if (n < 1 || n > (int64_t)INT32_MAX) return -3;
-  const int sh = (kout == k) ? 0 : 1;  // ffsrqr_plan has no l argument
-  if (k < 1 || k > n || k > m) return -4 - sh;
-  if (p < 0 || (int64_t)k + p > m || k + p > 256) return -5 - sh;
-  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64)
-    return -6 - sh;
-  if (opts && !(opts->g > 1.0)) return -7 - sh;
-  if (opts && opts->max_swaps < 0) return -7 - sh;
-  if (!workspace_bytes) return -8 - sh;
+// The plan for checked arguments: SRQR depth k, returned rank kout, TRQRCP
+// block size b (the sketch has b + p rows).
+int plan_create(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32_t k, int32_t b, int32_t p,
+                int32_t mode, const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
   const int elem = (mode == FFSRQR_FP64) ? 8 : 4;
   // the k x k factors live in one block's shared memory, and the row solves
   // hold at most 7 x 32 columns per lane group
@@ -1383,7 +1503,8 @@ int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32
   P->kout = kout;
   P->rsi_q = -1;  // Flip-Flop SRQR unless ffsrqr_plan_rsi says otherwise
   P->p = p;
-  P->s = k + p;
+  P->s = b + p;
+  P->blk = b;
   P->mode = mode;
   P->g = opts ? opts->g : 2.0;
   P->max_swaps = opts ? opts->max_swaps : 4 * k;
@@ -1433,6 +1554,55 @@ int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32
   return 0;
 }
 
+}  // namespace
+
+extern "C" {
+
+int ffsrqr_plan(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t p, int32_t mode,
+                const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  return ffsrqr_plan_l(plan, m, n, k, k, p, mode, opts, workspace_bytes);
+}
+
+int ffsrqr_plan_blocked(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t k, int32_t b, int32_t p, int32_t mode,
+                        const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (m < 1 || m > (int64_t)INT32_MAX) return -2;
+  if (n < 1 || n > (int64_t)INT32_MAX) return -3;
+  if (k < 1 || k > n || k > m) return -4;
+  if (b < 1 || b > k || (b < k && b % 8 != 0)) return -5;
+  if (p < 0 || (int64_t)b + p > m || b + p > 256) return -6;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64)
+    return -7;
+  if (opts && !(opts->g > 1.0)) return -8;
+  if (opts && opts->max_swaps < 0) return -8;
+  if (!workspace_bytes) return -9;
+  return plan_create(plan, m, n, k, k, b, p, mode, opts, workspace_bytes);
+}
+
+int ffsrqr_plan_l(ffsrqr_plan_t *plan, int64_t m, int64_t n, int32_t kout, int32_t k, int32_t p, int32_t mode,
+                  const ffsrqr_opts_t *opts, size_t *workspace_bytes) {
+  // here k is Alg. 9's SRQR depth l and kout its target rank; the checks
+  // below use ffsrqr_plan's argument numbers, shifted by one after kout
+  if (!plan) return -1;
+  *plan = nullptr;
+  if (kout < 1 || kout > k) {
+    if (k >= 1 && kout > k) return -5;
+    return -4;
+  }
+  if (m < 1 || m > (int64_t)INT32_MAX) return -2;
+  if (n < 1 || n > (int64_t)INT32_MAX) return -3;
+  const int sh = (kout == k) ? 0 : 1;  // ffsrqr_plan has no l argument
+  if (k < 1 || k > n || k > m) return -4 - sh;
+  if (p < 0 || (int64_t)k + p > m || k + p > 256) return -5 - sh;
+  if (mode != FFSRQR_PLAIN_FP32 && mode != FFSRQR_MIXED && mode != FFSRQR_MIXED_BF16X3 && mode != FFSRQR_FP64)
+    return -6 - sh;
+  if (opts && !(opts->g > 1.0)) return -7 - sh;
+  if (opts && opts->max_swaps < 0) return -7 - sh;
+  if (!workspace_bytes) return -8 - sh;
+  return plan_create(plan, m, n, kout, k, k, p, mode, opts, workspace_bytes);
+}
+
 int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,
                void *S, void *V, int64_t ldv, int32_t *piv, void *workspace, void *stream,
                ffsrqr_info_t *info) {
@@ -1477,6 +1647,13 @@ int ffsrqr_run(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, vo
   }
   plan->launches = g_launches;
   return rc;
+}
+
+int ffsrqr_plan_set_g2_rows(ffsrqr_plan_t plan, int32_t d) {
+  if (!plan) return -1;
+  if (d < 0 || d > G2EST_MAX_D) return -2;
+  if (plan->rsi_q >= 0) return FFSRQR_STATUS_UNSUPPORTED;
+  return plan->mode == FFSRQR_FP64 ? plan_g2_rows<double>(plan, d) : plan_g2_rows<float>(plan, d);
 }
 
 int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t seed, void *U, int64_t ldu,

@@ -60,6 +60,19 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &z0, d
   z1 = rad * sn;
 }
 
+// Element e of Gaussian stream `stream` under `seed` (the definition above),
+// one Philox block per call.
+template <typename T>
+__device__ __forceinline__ T gauss_elem(uint64_t seed, uint32_t stream, uint64_t e) {
+  const uint64_t q = e >> 2;
+  uint32_t c[4] = {(uint32_t)q, (uint32_t)(q >> 32), stream, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const bool hi = (e & 2u) != 0;
+  T z0, z1;
+  box_muller(hi ? c[2] : c[0], hi ? c[3] : c[1], z0, z1);
+  return (e & 1u) ? z1 : z0;
+}
+
 // Omega (s x m), row-major with leading dimension ldm; one thread per Philox
 // block (four consecutive stream elements).
 template <typename T>

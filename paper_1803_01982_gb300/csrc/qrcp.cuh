@@ -56,6 +56,10 @@ struct QrcpArgs {
   int stall_step;      // failure injection: this step's barrier waits for one block too many (-1: none)
   int cols_per_block;  // slab width (columns)
   int s_pad;           // slab column stride in shared memory
+  // columns already selected by an earlier TRQRCP block (nonzero entries are
+  // never pivots; may be sel itself: it is read before the first barrier,
+  // and written only after it); nullptr: none
+  const int *presel = nullptr;
 };
 
 // 16-byte vector of T in shared memory.
@@ -557,7 +561,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
       acc += x * x;
     }
     acc = warp_sum(acc);
-    if (lane == 0) nrm[c] = acc;
+    if (lane == 0) nrm[c] = (a.presel && a.presel[c0 + c]) ? T(-1) : acc;  // -1: selected
   }
   __syncthreads();
   if constexpr (sizeof(T) == 4) {

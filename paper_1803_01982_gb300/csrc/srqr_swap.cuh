@@ -26,13 +26,16 @@
 //      R(0:k, c), re-orthogonalised once, alpha = ||z||;
 //   f. R11^{-1} (warp-parallel back substitution), and the closed form
 //      g2 = max(1, max_i sqrt(alpha^2 ||e_i^T R11^{-1}||^2 + ((R11^{-1} a)_i)^2))
-//      with its maximising row imax (the next leaving position).
+//      with its maximising row imax (the next leaving position); or, with
+//      g2_rows = d >= 1, block 0 forms Alg. 4's d-row random estimate of the
+//      same column norms (g2est_block) and takes its maximum and argmax.
 // Reductions are done in fixed block order, so results do not depend on
 // timing.  A barrier that times out sets STATUS_TIMEOUT and every block
 // returns.
 #pragma once
 
 #include "common.cuh"
+#include "dense_small.cuh"
 
 namespace ffq {
 
@@ -63,6 +66,8 @@ struct SwapArgs {
   double g;
   int max_swaps;
   long long spin_limit;
+  int g2_rows;    // 0: exact g2; d >= 1: Alg. 4's d-row estimate
+  uint64_t seed;  // the run's seed (the estimate's Omega_t)
 };
 
 // R(t, col) for t <= k.
@@ -286,6 +291,38 @@ __global__ void __launch_bounds__(512) srqr_swap_kernel(SwapArgs<T> a) {
       s_sing = 0;
     }
     __syncthreads();
+    if (a.g2_rows > 0) {
+      // f (estimate). Block 0 draws Omega_t for test t = the new swap count
+      // and takes the estimated column norms; the others wait at the barrier.
+      if (b == 0) {
+        const int t = a.ctl[CTL_SWAPS] + 1;
+        const int zero = g2est_block<T>(a.Rd, k, as, s_alpha, k, a.g2_rows, a.seed, t, wacc);
+        const T *colsq = wacc + g2est_smem_elems(k) - k;
+        T bv = T(1);
+        int bi = 0x7fffffff;
+        for (int i = tid; i < k; i += nt) {
+          const T val = sqrt(colsq[i] / T(a.g2_rows));
+          if (better(val, i, bv, bi)) {
+            bv = val;
+            bi = i;
+          }
+        }
+        block_argmax(bv, bi, red_v, red_i);
+        if (tid == 0) {
+          const double g2 = zero ? 1.0 : (double)bv;
+          a.ctl[CTL_SWAPS] = t;
+          a.ctl[CTL_CAND] = c2;
+          a.ctl[CTL_IMAX] = (zero || bi == 0x7fffffff) ? -1 : bi;
+          a.dctl[D_G2] = g2;
+          a.dctl[D_ALPHA] = (double)s_alpha;
+          const bool need = g2 > a.g && a.ctl[CTL_IMAX] >= 0;
+          a.ctl[CTL_NEED_SWAP] = (need && t < a.max_swaps) ? 1 : 0;
+          if (need && t >= a.max_swaps) set_status(a.ctl, STATUS_SWAP_CAP);
+        }
+      }
+      if (!sync_grid()) return;
+      continue;
+    }
     // f. X = R11^{-1}: global warp gw solves R11 x = e_j for j = gw, gw + G*nwarp, ...
     for (int j = b * nwarp + wid; j < k; j += G * nwarp) {
       T *acc = wacc + wid * k;

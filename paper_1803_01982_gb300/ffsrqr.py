@@ -99,6 +99,9 @@ def _load():
     lib.ffsrqr_plan_rsi.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, i32, ctypes.POINTER(Opts),
                                     ctypes.POINTER(ctypes.c_size_t)]
     lib.ffsrqr_plan_rsi.restype = ctypes.c_int
+    lib.ffsrqr_plan_blocked.argtypes = [ctypes.POINTER(P), i64, i64, i32, i32, i32, i32, ctypes.POINTER(Opts),
+                                        ctypes.POINTER(ctypes.c_size_t)]
+    lib.ffsrqr_plan_blocked.restype = ctypes.c_int
     lib.ffsrqr_plan_depth.argtypes = [P]
     lib.ffsrqr_plan_depth.restype = ctypes.c_int
     lib.ffsrqr_run.argtypes = [P, P, i64, u64, P, i64, P, P, i64, P, P, P, ctypes.POINTER(Info)]
@@ -122,6 +125,8 @@ def _load():
     lib.ffsrqr_plan_tune.argtypes = [P, P, i64, ctypes.c_uint64, P, i64, P, P, i64, P, P, P, ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_float)]
     lib.ffsrqr_plan_tune.restype = ctypes.c_int
+    lib.ffsrqr_plan_set_g2_rows.argtypes = [P, i32]
+    lib.ffsrqr_plan_set_g2_rows.restype = ctypes.c_int
     lib.ffsrqr_launch_count.argtypes = [P]
     lib.ffsrqr_launch_count.restype = ctypes.c_int
     lib.ffsrqr_qrcp_static.argtypes = [P, i64, i32, i64, i32, P, P, P, P]
@@ -261,11 +266,13 @@ def _check(rc: int, what: str):
 class Plan:
     """Plan + device workspace for one (m, n, k, p, mode) shape; l (>= k) is
     Alg. 9's SRQR depth (None: l = k).  rsi_q (not None): the plan runs
-    randomized subspace iteration with that many iterations instead."""
+    randomized subspace iteration with that many iterations instead.  b (not
+    None): TRQRCP's block size (Alg. 2; the sketch has b + p rows).  g2_rows
+    (>= 1): Alg. 4's d-row random estimate of g2 instead of the exact one."""
 
     def __init__(self, m: int, n: int, k: int, p: int, mode: int = PLAIN_FP32, g: float = 2.0,
                  max_swaps: int | None = None, flags: int = 0, device=None, l: int | None = None,
-                 rsi_q: int | None = None):
+                 rsi_q: int | None = None, g2_rows: int = 0, b: int | None = None):
         import torch
         self.m, self.n, self.k, self.p, self.mode = m, n, k, p, mode
         self.device = torch.device("cuda" if device is None else device)
@@ -275,7 +282,11 @@ class Plan:
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t()
         with torch.cuda.device(self.device):
-            if rsi_q is not None:  # randomized subspace iteration with rsi_q iterations
+            if b is not None:  # TRQRCP with block size b (Alg. 2)
+                assert l is None and rsi_q is None
+                _check(lib.ffsrqr_plan_blocked(ctypes.byref(self._h), m, n, k, b, p, mode, ctypes.byref(opts),
+                                               ctypes.byref(ws)), "ffsrqr_plan_blocked")
+            elif rsi_q is not None:  # randomized subspace iteration with rsi_q iterations
                 _check(lib.ffsrqr_plan_rsi(ctypes.byref(self._h), m, n, k, p, rsi_q, mode, ctypes.byref(opts),
                                            ctypes.byref(ws)), "ffsrqr_plan_rsi")
             elif l is None:
@@ -284,12 +295,19 @@ class Plan:
             else:
                 _check(lib.ffsrqr_plan_l(ctypes.byref(self._h), m, n, k, l, p, mode, ctypes.byref(opts),
                                          ctypes.byref(ws)), "ffsrqr_plan_l")
+            if g2_rows:
+                self.set_g2_rows(g2_rows)
         self.workspace_bytes = ws.value
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
                                      device=self.device)
         base = self.workspace.data_ptr()
         self._ws_off = (-base) % 256
         self._info_host = torch.zeros(ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
+
+    def set_g2_rows(self, d: int) -> None:
+        """0: exact g2 in the SRQR test; d >= 1: Alg. 4's d-row random estimate."""
+        _check(lib.ffsrqr_plan_set_g2_rows(self._h, d), "ffsrqr_plan_set_g2_rows")
+        self.g2_rows = d
 
     @property
     def ws_ptr(self) -> int:
@@ -602,10 +620,17 @@ class Tucker:
         with torch.cuda.device(self.device):
             _check(lib.ffsrqr_tucker_plan(ctypes.byref(self._h), method, d, dims_c, ranks_c, order_c, p, mode,
                                           ctypes.byref(opts), ctypes.byref(ws)), "ffsrqr_tucker_plan")
+            if g2_rows:
+                self.set_g2_rows(g2_rows)
         self.workspace_bytes = ws.value
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         self._ws_off = (-self.workspace.data_ptr()) % 256
         self._info_host = torch.zeros(d * ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
+
+    def set_g2_rows(self, d: int) -> None:
+        """0: exact g2 in the SRQR test; d >= 1: Alg. 4's d-row random estimate."""
+        _check(lib.ffsrqr_plan_set_g2_rows(self._h, d), "ffsrqr_plan_set_g2_rows")
+        self.g2_rows = d
 
     @property
     def ws_ptr(self) -> int:
@@ -667,6 +692,8 @@ class RPCA:
         with torch.cuda.device(self.device):
             _check(lib.ffsrqr_rpca_create(ctypes.byref(self._h), m, n, ctypes.byref(opts), ctypes.byref(ws)),
                    "ffsrqr_rpca_create")
+            if g2_rows:
+                self.set_g2_rows(g2_rows)
         self.workspace_bytes = ws.value
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         self._ws_off = (-self.workspace.data_ptr()) % 256

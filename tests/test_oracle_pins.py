@@ -263,6 +263,139 @@ def test_swap_cap_status():
 
 
 # --------------------------------------------------------------------------
+# Alg. 2 (TRQRCP) with block size b < k
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("b", [1, 5, 8, 12])
+def test_blocked_pivots_are_lapack_qrcp_of_the_trailing_sample(b):
+    # block j's pivots = the first bb pivots of LAPACK's QRCP (geqp3) of the
+    # sample of the trailing matrix, Omega (I - P_j P_j^T) A restricted to the
+    # unselected columns, with P_j an orthonormal basis (numpy QR) of the
+    # columns chosen by the earlier blocks
+    rng = np.random.default_rng(b)
+    m, n, k, p = 160, 120, 20, 6
+    A = synth.decayed(m, n, 0.9 ** np.arange(n), 1e-3, seed=10 + b, dtype=np.float64)
+    A = A * np.exp(0.3 * rng.standard_normal(n))[None, :]
+    B = _sketch(A, b + p)
+    res = oracle.srqr(A, B, k, g=1e300, b=b)
+    Om = oracle.omega(0, b + p, m)
+    for jb in range(0, k, b):
+        bb = min(b, k - jb)
+        chosen = list(res.perm0[:jb])
+        rest = [i for i in range(n) if i not in chosen]
+        T = A[:, rest]
+        if chosen:
+            P, _ = np.linalg.qr(A[:, chosen])
+            T = T - P @ (P.T @ T)
+        _, _, piv = scipy.linalg.qr(Om @ T, pivoting=True, mode="economic")
+        assert [rest[i] for i in piv[:bb]] == list(res.perm0[jb:jb + bb]), jb
+    # the unselected columns follow in ascending order
+    assert list(res.perm0[k:]) == sorted(set(range(n)) - set(res.perm0[:k]))
+
+
+@pytest.mark.parametrize("b", [1, 4, 7])
+def test_blocked_ffsrqr_exact_on_rank_k(b):
+    k = 9
+    A = synth.rank_k(70, 55, k, seed=5)
+    r = oracle.ffsrqr(A, k, 4, seed=3, b=b)
+    s_true = np.linalg.svd(A, compute_uv=False)
+    np.testing.assert_allclose(r.S, s_true[:k], rtol=1e-10)
+    assert oracle.residual_fro(A, r.U, r.S, r.V) < 1e-11 * s_true[0]
+
+
+def test_blocked_ffsrqr_equals_rayleigh_ritz_closed_form():
+    A = synth.decayed(90, 70, 0.85 ** np.arange(70), 1e-3, seed=6, dtype=np.float64)
+    k, p, b = 14, 5, 6
+    r = oracle.ffsrqr(A, k, p, seed=2, b=b, g=1e300)
+    U, S, V = _ritz(A, r.piv[:k], k)
+    np.testing.assert_allclose(r.S, S, rtol=1e-10)
+    np.testing.assert_allclose(np.abs(r.U.T @ U), np.eye(k), atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# Alg. 4's d-row random estimate of g2
+# --------------------------------------------------------------------------
+def _g2_omega(seed, t, d, kp):
+    """Omega_t (d x (l+1)) of the estimate: element (r, j) is element
+    (t d + r)(l+1) + j of Philox stream 1 (the stream is pinned above)."""
+    return np.array([[oracle.normal(seed, 1, (t * d + r) * kp + j) for j in range(kp)]
+                     for r in range(d)])
+
+
+@pytest.mark.parametrize("d", [1, 3, 8])
+def test_g2_estimate_on_orthogonal_columns(d):
+    # A = Q diag(sigma) with orthonormal Q: R11 = diag(sigma of the pivots), a = 0
+    # and alpha = sigma of the candidate, so column i of |alpha| Omega Rtilde^{-T}
+    # is (alpha / R_ii) Omega(:, i): the estimate needs no inverse at all.
+    rng = np.random.default_rng(5)
+    m, n, k, p = 70, 40, 9, 4
+    sig = 0.8 ** rng.permutation(n)
+    Q, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    A = Q * sig[None, :]
+    res = oracle.srqr(A, _sketch(A, k + p), k, g=1e300, g2_rows=d, seed=11)
+    assert res.swaps == 0
+    piv, c = res.perm[:k], res.cand_first
+    Om = _g2_omega(11, 0, d, k + 1)
+    terms = sig[c] / sig[piv] * np.linalg.norm(Om[:, :k], axis=0) / math.sqrt(d)
+    assert res.alpha_first == pytest.approx(sig[c], rel=1e-12)
+    assert res.g2_first == pytest.approx(max(1.0, terms.max()), rel=1e-10)
+
+
+def test_g2_estimate_matches_explicit_inverse():
+    A = synth.decayed(100, 70, 0.85 ** np.arange(70), 1e-3, seed=4, dtype=np.float64)
+    k, p, d = 12, 5, 4
+    res = oracle.srqr(A, _sketch(A, k + p), k, g=1e300, g2_rows=d, seed=3)
+    Rt = np.zeros((k + 1, k + 1))
+    Rt[:k, :k] = res.R[:, :k]
+    Rt[:k, k] = res.R[:, k]
+    Rt[k, k] = res.alpha_first
+    Y = _g2_omega(3, 0, d, k + 1) @ np.linalg.inv(Rt).T
+    est = res.alpha_first * np.linalg.norm(Y, axis=0) / math.sqrt(d)
+    assert res.g2_first == pytest.approx(max(1.0, est[:k].max()), rel=1e-9)
+
+
+def test_g2_estimate_converges_to_exact():
+    # E ||Omega x||^2 = d ||x||^2: with many rows the estimate approaches the
+    # exact g2 (relative spread about 1/sqrt(2d) per column)
+    A = synth.decayed(100, 70, 0.85 ** np.arange(70), 1e-3, seed=4, dtype=np.float64)
+    k, p = 12, 5
+    B = _sketch(A, k + p)
+    exact = oracle.srqr(A, B, k, g=1e300).g2_first
+    est = oracle.srqr(A, B, k, g=1e300, g2_rows=20000, seed=1).g2_first
+    assert exact > 1.1  # not the floor of 1
+    assert est == pytest.approx(exact, rel=0.02)
+
+
+def test_g2_estimate_is_scale_invariant():
+    # g2 is homogeneous of degree 0 in A: alpha scales like R11, so the same
+    # Omega_t gives the same estimate and the same swap decisions
+    n = 48
+    K = synth.kahan(n, 0.285) * (1.0 + 1e-10 * np.arange(n))[None, :]
+    k, p = 30, 6
+    B = _sketch(K, k + p)
+    r1 = oracle.srqr(K, B, k, g=1.05, g2_rows=3, seed=2)
+    r2 = oracle.srqr(1e3 * K, 1e3 * B, k, g=1.05, g2_rows=3, seed=2)
+    assert r1.swaps == r2.swaps > 0
+    assert list(r1.perm) == list(r2.perm)
+    assert r2.g2_first == pytest.approx(r1.g2_first, rel=1e-11)
+    assert r2.g2_final == pytest.approx(r1.g2_final, rel=1e-11)
+
+
+@pytest.mark.parametrize("d", [1, 4])
+def test_swap_loop_with_g2_estimate(d):
+    n = 48
+    K = synth.kahan(n, 0.285) * (1.0 + 1e-10 * np.arange(n))[None, :]
+    k, p = 30, 6
+    res = oracle.srqr(K, _sketch(K, k + p), k, g=1.05, g2_rows=d, seed=0)
+    assert res.swaps > 0
+    assert res.g2_final <= 1.05 or res.status == 2
+    Ap = K[:, res.perm]
+    np.testing.assert_allclose(res.Q1 @ res.R[:, :k], Ap[:, :k], atol=1e-12)
+    np.testing.assert_allclose(res.R, res.Q1.T @ Ap, atol=1e-12)
+    np.testing.assert_allclose(res.Q1.T @ res.Q1, np.eye(k), atol=1e-12)
+    assert sorted(res.perm) == list(range(n))
+
+
+# --------------------------------------------------------------------------
 # Flip-Flop SRQR (Alg. 9)
 # --------------------------------------------------------------------------
 def _ritz(A, J, k):
