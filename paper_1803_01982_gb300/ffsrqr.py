@@ -620,17 +620,10 @@ class Tucker:
         with torch.cuda.device(self.device):
             _check(lib.ffsrqr_tucker_plan(ctypes.byref(self._h), method, d, dims_c, ranks_c, order_c, p, mode,
                                           ctypes.byref(opts), ctypes.byref(ws)), "ffsrqr_tucker_plan")
-            if g2_rows:
-                self.set_g2_rows(g2_rows)
         self.workspace_bytes = ws.value
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         self._ws_off = (-self.workspace.data_ptr()) % 256
         self._info_host = torch.zeros(d * ctypes.sizeof(Info), dtype=torch.uint8).pin_memory()
-
-    def set_g2_rows(self, d: int) -> None:
-        """0: exact g2 in the SRQR test; d >= 1: Alg. 4's d-row random estimate."""
-        _check(lib.ffsrqr_plan_set_g2_rows(self._h, d), "ffsrqr_plan_set_g2_rows")
-        self.g2_rows = d
 
     @property
     def ws_ptr(self) -> int:
@@ -692,8 +685,6 @@ class RPCA:
         with torch.cuda.device(self.device):
             _check(lib.ffsrqr_rpca_create(ctypes.byref(self._h), m, n, ctypes.byref(opts), ctypes.byref(ws)),
                    "ffsrqr_rpca_create")
-            if g2_rows:
-                self.set_g2_rows(g2_rows)
         self.workspace_bytes = ws.value
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         self._ws_off = (-self.workspace.data_ptr()) % 256
