@@ -538,18 +538,36 @@ __global__ void __launch_bounds__(256) trailing_norms_kernel(const T *__restrict
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   T bv = neg_inf<T>();
   int bi = 0x7fffffff;
-  for (int64_t i = (int64_t)blockIdx.x * nwarp + wid; i < n; i += (int64_t)gridDim.x * nwarp) {
-    T acc = T(0);
+  // a warp per column, CPI columns per iteration so that their loads are in
+  // flight together
+  constexpr int CPI = 4;
+  const int64_t stride = (int64_t)gridDim.x * nwarp;
+  for (int64_t i0 = (int64_t)blockIdx.x * nwarp + wid; i0 < n; i0 += CPI * stride) {
+    T acc[CPI];
+#pragma unroll
+    for (int q = 0; q < CPI; ++q) acc[q] = T(0);
     for (int t = lane; t < s; t += 32) {
-      const T d = Bt[i * lds + t] - CBt[i * lds + t];
-      acc = fma(d, d, acc);
+#pragma unroll
+      for (int q = 0; q < CPI; ++q) {
+        const int64_t i = i0 + q * stride;
+        if (i < n) {
+          const T d = Bt[i * lds + t] - CBt[i * lds + t];
+          acc[q] = fma(d, d, acc[q]);
+        }
+      }
     }
-    acc = warp_sum(acc) / T(s);
-    const bool inJ = sel[i] != 0;
-    if (lane == 0) r[i] = inJ ? T(0) : acc;
-    if (!inJ && better(acc, (int)i, bv, bi)) {
-      bv = acc;
-      bi = (int)i;
+#pragma unroll
+    for (int q = 0; q < CPI; ++q) {
+      const int64_t i = i0 + q * stride;
+      const T a = warp_sum(acc[q]) / T(s);
+      if (i < n) {
+        const bool inJ = sel[i] != 0;
+        if (lane == 0) r[i] = inJ ? T(0) : a;
+        if (!inJ && better(a, (int)i, bv, bi)) {
+          bv = a;
+          bi = (int)i;
+        }
+      }
     }
   }
   block_argmax(bv, bi, red_v, red_i);
@@ -655,46 +673,69 @@ __global__ void __launch_bounds__(256) srqr_resid_kernel(const T *__restrict__ A
   }
 }
 
-// z -= Q1 h (h = sum of block partials), partial ||z||^2 per block.
+// h = sum over the nhp block partials of srqr_resid_kernel (k entries), in a
+// fixed order: one block; G = blockDim / k groups, group g adds the partials
+// g, g + G, ... (loads unrolled, so several are in flight), then the groups'
+// sums are added in group order.  The reorthogonalisation's blocks then read h
+// instead of each reducing all partials on a chain of dependent loads.
+template <typename T>
+__global__ void __launch_bounds__(1024) srqr_hsum_kernel(const T *__restrict__ hpart, int nhp, int k,
+                                                         const int *ctl, T *__restrict__ h) {
+  __shared__ T part[1024];
+  if (ctl[CTL_CAND] == 0x7fffffff) return;
+  const int G = max(1, (int)blockDim.x / k);
+  const int t = threadIdx.x, g = t / k, j = t - g * k;
+  if (g < G) {
+    T acc = T(0);
+#pragma unroll 8
+    for (int b = g; b < nhp; b += G) acc += hpart[(int64_t)b * k + j];
+    part[t] = acc;
+  }
+  __syncthreads();
+  for (int jj = t; jj < k; jj += blockDim.x) {
+    T acc = T(0);
+    for (int gg = 0; gg < G; ++gg) acc += part[gg * k + jj];
+    h[jj] = acc;
+  }
+}
+
+// z -= Q1 h (h from srqr_hsum_kernel), partial ||z||^2 per block.
 template <typename T>
 __global__ void __launch_bounds__(256) srqr_reorth_kernel(int64_t m, const T *__restrict__ Q1,
-                                                          int64_t ldq, int k,
-                                                          const T *__restrict__ hpart, int nhp,
+                                                          int64_t ldq, int k, const T *__restrict__ h,
                                                           const int *ctl, T *__restrict__ z,
                                                           T *__restrict__ npart) {
   constexpr int SR_ROWS = 4, NJ = 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *hs = reinterpret_cast<T *>(smem_raw);
   __shared__ T red[32];
   if (ctl[CTL_CAND] == 0x7fffffff) return;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    T acc = T(0);
-    for (int b = 0; b < nhp; ++b) acc += hpart[(int64_t)b * k + j];
-    hs[j] = acc;
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   T hv[NJ];
 #pragma unroll
   for (int u = 0; u < NJ; ++u) {
     const int j = lane + 32 * u;
-    hv[u] = (j < k) ? hs[j] : T(0);
+    hv[u] = (j < k) ? h[j] : T(0);
   }
   const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * rows_per, i1 = min(m, i0 + rows_per);
   T nacc = T(0);
   for (int64_t base = i0 + (int64_t)wid * SR_ROWS; base < i1; base += (int64_t)nwarp * SR_ROWS) {
-    T acc[SR_ROWS], zz[SR_ROWS];
+    // all of the rows' loads first (in flight together), then the products
+    T q[SR_ROWS][NJ], acc[SR_ROWS], zz[SR_ROWS];
 #pragma unroll
     for (int r = 0; r < SR_ROWS; ++r) {
       const int64_t i = base + r;
-      acc[r] = T(0);
       zz[r] = (i < i1) ? z[i] : T(0);
 #pragma unroll
       for (int u = 0; u < NJ; ++u) {
         const int j = lane + 32 * u;
-        if (i < i1 && j < k) acc[r] = fma(Q1[i * ldq + j], hv[u], acc[r]);
+        q[r][u] = (i < i1 && j < k) ? Q1[i * ldq + j] : T(0);
       }
+    }
+#pragma unroll
+    for (int r = 0; r < SR_ROWS; ++r) {
+      acc[r] = T(0);
+#pragma unroll
+      for (int u = 0; u < NJ; ++u) acc[r] = fma(q[r][u], hv[u], acc[r]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -720,7 +761,8 @@ __global__ void __launch_bounds__(256) srqr_reorth_kernel(int64_t m, const T *__
 // ((R11^{-1} a)_i)^2)) -- the closed form of |alpha| ||Rtilde^{-T}||_{1,2}
 // (Sec. 2.2); R11^{-1} a = Zt[c, :].  Rinv = R11^{-1} (k x k).
 template <typename T>
-__global__ void srqr_g2_kernel(const T *__restrict__ npart, int nnp, const T *__restrict__ Rinv,
+__global__ void __launch_bounds__(512) srqr_g2_kernel(const T *__restrict__ npart, int nnp,
+                                                       const T *__restrict__ Rinv,
                                int k, const T *__restrict__ Zt, int64_t ldz, double g, int max_swaps,
                                int *ctl, double *dctl, int first) {
   __shared__ T red_v[32];
@@ -735,21 +777,25 @@ __global__ void srqr_g2_kernel(const T *__restrict__ npart, int nnp, const T *__
     }
     return;
   }
-  if (threadIdx.x == 0) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (wid == 0) {  // alpha^2 = sum of the block partials, lanes in order then a fixed tree
     T acc = T(0);
-    for (int b = 0; b < nnp; ++b) acc += npart[b];
-    s_alpha = sqrt(acc);
+    for (int b = lane; b < nnp; b += 32) acc += npart[b];
+    acc = warp_sum(acc);
+    if (lane == 0) s_alpha = sqrt(acc);
   }
   __syncthreads();
   const T alpha = s_alpha;
   T bv = T(1);
   int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+  // a warp per row i of R11^{-1}: coalesced loads of its entries j >= i
+  for (int i = wid; i < k; i += nwarp) {
     T rn = T(0);
-    for (int j = i; j < k; ++j) rn = fma(Rinv[i * k + j], Rinv[i * k + j], rn);
+    for (int j = i + lane; j < k; j += 32) rn = fma(Rinv[i * k + j], Rinv[i * k + j], rn);
+    rn = warp_sum(rn);
     const T u = Zt[(int64_t)c * ldz + i];
     const T val = sqrt(alpha * alpha * rn + u * u);
-    if (better(val, i, bv, bi)) {
+    if (lane == 0 && better(val, i, bv, bi)) {
       bv = val;
       bi = i;
     }
@@ -886,10 +932,11 @@ __global__ void __launch_bounds__(1024) srqr_g2est_kernel(const T *__restrict__ 
     }
     return;
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {  // alpha^2 = sum of the block partials (as srqr_g2_kernel)
     T acc = T(0);
-    for (int b = 0; b < nnp; ++b) acc += npart[b];
-    s_alpha = sqrt(acc);
+    for (int b = threadIdx.x; b < nnp; b += 32) acc += npart[b];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) s_alpha = sqrt(acc);
   }
   __syncthreads();
   const T alpha = s_alpha;

@@ -511,8 +511,11 @@ int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A,
   srqr_resid_kernel<T><<<P->nblk_res, threads, smem1, st>>>(A, lda, P->m, w.q1, P->ldk, k, w.avec,
                                                             w.ctl, w.z, w.hpart);
   CKL("srqr_resid");
-  srqr_reorth_kernel<T><<<P->nblk_res, threads, (size_t)k * sizeof(T), st>>>(
-      P->m, w.q1, P->ldk, k, w.hpart, P->nblk_res, w.ctl, w.z, w.npart);
+  // h = Q1^T z: the block partials added once, into the row after them
+  T *h = w.hpart + (size_t)P->nblk_res * k;
+  srqr_hsum_kernel<T><<<1, 1024, 0, st>>>(w.hpart, P->nblk_res, k, w.ctl, h);
+  CKL("srqr_hsum");
+  srqr_reorth_kernel<T><<<P->nblk_res, threads, 0, st>>>(P->m, w.q1, P->ldk, k, h, w.ctl, w.z, w.npart);
   CKL("srqr_reorth");
   if (P->g2_rows > 0) {
     srqr_g2est_kernel<T><<<1, 1024, (size_t)g2est_smem_elems(k) * sizeof(T), st>>>(
@@ -520,7 +523,7 @@ int srqr_test(cudaStream_t st, const ffsrqr_plan_s *P, WsPtrs<T> &w, const T *A,
     CKL("srqr_g2est");
     return 0;
   }
-  srqr_g2_kernel<T><<<1, 256, 0, st>>>(w.npart, P->nblk_res, w.rinv, k, w.zt, P->ldk, P->g,
+  srqr_g2_kernel<T><<<1, 512, 0, st>>>(w.npart, P->nblk_res, w.rinv, k, w.zt, P->ldk, P->g,
                                        P->max_swaps, w.ctl, w.dctl, first);
   CKL("srqr_g2");
   return 0;
@@ -1305,7 +1308,7 @@ void layout(ffsrqr_plan_s *P) {
   P->off_avec = take((size_t)k * E);
   P->off_z = take((size_t)m * E);
   P->nblk_res = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 64), nsm));
-  P->off_hpart = take((size_t)P->nblk_res * k * E);
+  P->off_hpart = take((size_t)(P->nblk_res + 1) * k * E);  // block partials of h, then h
   P->off_npart = take((size_t)P->nblk_res * E);
   P->off_vp = take((size_t)n * ldk * E);
   P->off_rz = take((size_t)k * k * E);
