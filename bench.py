@@ -310,6 +310,7 @@ def run_ours(a, rank, world, local_rank):
     clocks = clocks_stop(clk, clk_path)
     ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
     info = plan.info()
+    qrcp_barriers = int(plan.item("ctl")[0, 38].item())  # grid barriers of the sketch QRCP
     value = world * 1000.0 / ms
     phases = {k: v / a.steps for k, v in phase_sum.items()}
 
@@ -373,7 +374,8 @@ def run_ours(a, rank, world, local_rank):
                 "modes": {k: {kk: vv for kk, vv in v.items() if kk != "out"} for k, v in modes.items()}
                 if modes else None,
                 "clocks": clocks, "phases_ms": {k: round(v, 4) for k, v in phases.items()},
-                "status": info["status"], "swaps": info["swaps"], "g2": info["g2_first"]}
+                "status": info["status"], "swaps": info["swaps"], "g2": info["g2_first"],
+                "qrcp_barriers": qrcp_barriers}
         print(json.dumps(line), flush=True)
 
 

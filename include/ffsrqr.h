@@ -233,7 +233,8 @@ int ffsrqr_plan_tune(ffsrqr_plan_t plan, const void *A, int64_t lda, uint64_t se
  * (m x k), 7 trailing estimates r (n), 8 M_t (k x k, tmp = Q_t M_t), 9 the
  * device control words (1 x 40 int32: status, counters; words 14 and 15
  * count the second Cholesky-QR sweeps that took the first-order expansion of
- * their factor and the exact factorization).
+ * their factor and the exact factorization; word 38 the grid barriers of the
+ * single-precision sketch QRCP).
  * Writes the byte offset, row/column counts and leading dimension (elements)
  * and the element size in bytes.  Returns 0 or -2 for an unknown item. */
 int ffsrqr_workspace_item(ffsrqr_plan_t plan, int32_t what, size_t *offset, int64_t *rows,

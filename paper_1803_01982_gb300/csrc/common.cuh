@@ -28,6 +28,7 @@ enum CtlSlot : int {
   CTL_SERIES_EXACT = 15,  // second sweeps that took the exact factorization
   CTL_SWEEP_ROT0 = 16,  // rotations performed in Jacobi sweeps 0..15 (diagnostic)
   CTL_WIN_KEY = 32,     // 3 x uint64 (words 32..37): QRCP winner keys, one per step mod 3
+  CTL_QRCP_BARRIERS = 38,  // grid barriers the single-precision QRCP took (diagnostic)
   CTL_WORDS = 40,
 };
 

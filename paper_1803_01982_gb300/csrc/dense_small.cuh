@@ -788,16 +788,34 @@ __global__ void __launch_bounds__(512) srqr_g2_kernel(const T *__restrict__ npar
   const T alpha = s_alpha;
   T bv = T(1);
   int bi = 0x7fffffff;
-  // a warp per row i of R11^{-1}: coalesced loads of its entries j >= i
-  for (int i = wid; i < k; i += nwarp) {
-    T rn = T(0);
-    for (int j = i + lane; j < k; j += 32) rn = fma(Rinv[i * k + j], Rinv[i * k + j], rn);
-    rn = warp_sum(rn);
-    const T u = Zt[(int64_t)c * ldz + i];
-    const T val = sqrt(alpha * alpha * rn + u * u);
-    if (lane == 0 && better(val, i, bv, bi)) {
-      bv = val;
-      bi = i;
+  // a warp per row i of R11^{-1} (coalesced loads of its entries j >= i),
+  // G2_RPW rows at a time so that their loads are in flight together
+  constexpr int G2_RPW = 4;
+  for (int i0 = wid; i0 < k; i0 += G2_RPW * nwarp) {
+    T rn[G2_RPW];
+#pragma unroll
+    for (int r = 0; r < G2_RPW; ++r) {
+      const int i = i0 + r * nwarp;
+      rn[r] = T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {  // k <= 256
+        const int j = lane + 32 * u;
+        const T x = (i < k && j >= i && j < k) ? Rinv[i * k + j] : T(0);
+        rn[r] = fma(x, x, rn[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < G2_RPW; ++r) {
+      const int i = i0 + r * nwarp;
+      const T sq = warp_sum(rn[r]);
+      if (i < k) {
+        const T u = Zt[(int64_t)c * ldz + i];
+        const T val = sqrt(alpha * alpha * sq + u * u);
+        if (lane == 0 && better(val, i, bv, bi)) {
+          bv = val;
+          bi = i;
+        }
+      }
     }
   }
   block_argmax(bv, bi, red_v, red_i);

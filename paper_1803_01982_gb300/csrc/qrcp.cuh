@@ -19,17 +19,20 @@
 //      H = I - tau v v^T from B(j:s, p) (beta = -sign(x_j) ||x||);
 //   4. each block applies H to its own unselected columns and recomputes their
 //      trailing norms ||B(j+1:s, i)||^2 exactly (no downdating).
-// Single precision takes up to two pivots per grid barrier: besides its best
-// column every block publishes a bound, the largest trailing norm among its
-// other columns.  After the barrier every block applies the winner's
-// reflector H_j to the published candidates whose norm exceeds the largest
-// bound (at most QRCP_MAXC of them, read from the candidate copies) and takes
-// the best updated norm: trailing norms only shrink under H_j, so if that
-// norm exceeds every bound no other column can reach it, and it is step
-// j + 1's greedy winner -- taken at once, with both reflectors applied to
-// the slabs in one pass.  Every block computes the same certificate from the
-// same published data, so all take the same decision.  On the benchmark
-// sketches about 90 % of the barriers certify a second pivot.
+// Single precision takes up to QRCP_MAXP pivots per grid barrier: besides
+// its best column every block publishes a bound, the largest trailing norm
+// among its other columns.  After the barrier every block applies the
+// winner's reflector H_j to the published candidates whose norm exceeds the
+// largest bound (at most QRCP_MAXC of them, read from the candidate copies)
+// and takes the best updated norm: trailing norms only shrink under the
+// reflectors, so if that norm exceeds every bound no other column can reach
+// it, and it is step j + 1's greedy winner.  The same test is repeated with
+// H_{j+1} applied to the remaining candidates, and so on, until a best norm
+// fails the test or QRCP_MAXP pivots are taken; all of the barrier's
+// reflectors are then applied to the slabs in one pass.  Every block computes
+// the same certificates from the same published data, so all take the same
+// decisions.  On the benchmark sketch (k = 200) the barriers fall from 108
+// (at most two pivots each) to about 70.
 // Outputs: piv[0:k] (original indices, in pivot order), S11 (k x k, row-major,
 // the R factor of the pivoted sketch columns: S11(0:j, j) = transformed pivot
 // column above the diagonal, S11(j, j) = beta), status RANK_DEFICIENT if a
@@ -139,60 +142,78 @@ __device__ __forceinline__ void apply_reflector_lanes(T *slab, int ld, int ncol,
   }
 }
 
-constexpr int QRCP_MAXC = 48;  // candidate columns evaluated for a second pivot per barrier
+constexpr int QRCP_MAXC = 48;  // candidate columns evaluated for further pivots per barrier
 constexpr int QRCP_CPW = 3;    // of which one warp of 16 evaluates up to three
+constexpr int QRCP_MAXP = 4;   // pivots taken per barrier at most (single precision)
 
 // Shared-memory floats past the slab and its norms in single precision: the
-// second reflector and the QRCP_MAXC candidate columns after H_j.
-__host__ __device__ inline int qrcp_pair_extra(int s_pad) { return (1 + QRCP_MAXC) * s_pad; }
+// reflectors 2 .. QRCP_MAXP of a barrier and the QRCP_MAXC candidate columns.
+__host__ __device__ inline int qrcp_pair_extra(int s_pad) { return (QRCP_MAXP - 1 + QRCP_MAXC) * s_pad; }
 
-// H2 H1 applied to the block's columns (H1 = I - tau1 v1 v1^T from row j,
-// H2 from row j + 1) in one read pass and one update pass:
-//   H2 H1 x = x - w1 v1 - w2 v2, w1 = tau1 v1.x, w2 = tau2 (v2.x - w1 v2.v1),
-// trailing norms over rows > j + 1 recomputed; LPC lanes per column as in
-// apply_reflector_lanes.  c12 = v2.v1.
-template <int LPC>
-__device__ __forceinline__ void apply_two_reflectors_lanes(float *slab, int ld, int ncol, const float *v1, float tau1,
-                                                           const float *v2, float tau2, float c12, int j,
-                                                           float *nrm) {
+// H_P ... H_1 applied to the block's columns (H_i = I - tau_i v_i v_i^T from
+// row j + i - 1) in one read pass and one update pass:
+//   H_P ... H_1 x = x - sum_i w_i v_i,  w_i = tau_i (v_i.x - sum_{l<i} (v_i.v_l) w_l),
+// trailing norms over rows > j + P - 1 recomputed; LPC lanes per column as in
+// apply_reflector_lanes.  cc[i][l] = v_i.v_l for l < i.
+template <int P, int LPC>
+__device__ __forceinline__ void apply_reflectors_lanes(float *slab, int ld, int ncol, float *const *vp,
+                                                       const float *tau, const float (*cc)[QRCP_MAXP], int j,
+                                                       float *nrm) {
   constexpr int VN = 4;
   constexpr int CPW = 32 / LPC;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int gl = lane % LPC;
   const int q0 = j / VN, nq = ld / VN;
+  const int jn = j + P - 1;  // norms over rows > jn
+  const float *vv[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) vv[i] = vp[i];
   for (int base = wid * CPW; base < ncol; base += nwarp * CPW) {  // warp-uniform
     const int c = base + lane / LPC;
     const bool on = c < ncol;
     float *col = slab + (size_t)(on ? c : 0) * ld;
-    float d1 = 0.f, d2 = 0.f;
+    float d[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) d[i] = 0.f;
     if (on)
-#pragma unroll 4
+#pragma unroll 2
       for (int q = q0 + gl; q < nq; q += LPC) {
-        const float4 vv = *reinterpret_cast<const float4 *>(v1 + q * VN);
-        const float4 uu = *reinterpret_cast<const float4 *>(v2 + q * VN);
         const float4 xx = *reinterpret_cast<const float4 *>(col + q * VN);
-        d1 = fmaf(vv.x, xx.x, fmaf(vv.y, xx.y, fmaf(vv.z, xx.z, fmaf(vv.w, xx.w, d1))));
-        d2 = fmaf(uu.x, xx.x, fmaf(uu.y, xx.y, fmaf(uu.z, xx.z, fmaf(uu.w, xx.w, d2))));
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const float4 u = *reinterpret_cast<const float4 *>(vv[i] + q * VN);
+          d[i] = fmaf(u.x, xx.x, fmaf(u.y, xx.y, fmaf(u.z, xx.z, fmaf(u.w, xx.w, d[i]))));
+        }
       }
 #pragma unroll
-    for (int o = LPC / 2; o > 0; o >>= 1) {
-      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    for (int o = LPC / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int i = 0; i < P; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+    float w[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      float t = d[i];
+#pragma unroll
+      for (int l = 0; l < i; ++l) t = fmaf(-cc[i][l], w[l], t);
+      w[i] = tau[i] * t;
     }
-    const float w1 = tau1 * d1;
-    const float w2 = tau2 * fmaf(-w1, c12, d2);
     float acc = 0.f;
     if (on)
-#pragma unroll 4
+#pragma unroll 2
       for (int q = q0 + gl; q < nq; q += LPC) {
-        const float4 vv = *reinterpret_cast<const float4 *>(v1 + q * VN);
-        const float4 uu = *reinterpret_cast<const float4 *>(v2 + q * VN);
         const float4 xx = *reinterpret_cast<const float4 *>(col + q * VN);
-        const float y[4] = {fmaf(-w2, uu.x, fmaf(-w1, vv.x, xx.x)), fmaf(-w2, uu.y, fmaf(-w1, vv.y, xx.y)),
-                            fmaf(-w2, uu.z, fmaf(-w1, vv.z, xx.z)), fmaf(-w2, uu.w, fmaf(-w1, vv.w, xx.w))};
+        float y[4] = {xx.x, xx.y, xx.z, xx.w};
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const float4 u = *reinterpret_cast<const float4 *>(vv[i] + q * VN);
+          y[0] = fmaf(-w[i], u.x, y[0]);
+          y[1] = fmaf(-w[i], u.y, y[1]);
+          y[2] = fmaf(-w[i], u.z, y[2]);
+          y[3] = fmaf(-w[i], u.w, y[3]);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (q * VN + e > j + 1) acc = fmaf(y[e], y[e], acc);
+          if (q * VN + e > jn) acc = fmaf(y[e], y[e], acc);
         *reinterpret_cast<float4 *>(col + q * VN) = make_float4(y[0], y[1], y[2], y[3]);
       }
 #pragma unroll
@@ -257,10 +278,16 @@ __device__ __forceinline__ void block_top2(float &v1, int &i1, float &v2, float 
 constexpr int QRCP_TAB = 8;   // candidate-table entries per lane (grid <= 256)
 constexpr int QRCP_COL = 8;   // column entries per lane (s_pad <= 256)
 __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *slab, float *v, float *nrm,
-                                               float *v2, float *ybuf, int64_t c0, int ncol) {
+                                               float *vx, int64_t c0, int ncol) {
+  // reflector i of a barrier: v (the winner's), then the QRCP_MAXP - 1 vectors
+  // at vx; the candidate columns after them
+  auto vpt = [&](int i) { return (i == 0) ? v : vx + (size_t)(i - 1) * a.s_pad; };
+  float *ybuf = vx + (size_t)(QRCP_MAXP - 1) * a.s_pad;
   __shared__ float red_v[32], red_2[32];
   __shared__ int red_i[32];
-  __shared__ float s_tau, s_beta, s_scal, s_wv, s_bound, s_tau2, s_c12;
+  __shared__ float s_tau, s_beta, s_scal, s_wv, s_bound;
+  __shared__ float s_tl[QRCP_MAXP];             // tau of the barrier's reflectors
+  __shared__ float s_cc[QRCP_MAXP][QRCP_MAXP];  // v_i . v_l, l < i
   __shared__ int s_win_blk, s_win_col, s_ncand, s_pair;
   __shared__ int s_cblk[QRCP_MAXC], s_cidx[QRCP_MAXC];
   __shared__ float s_cnn[QRCP_MAXC];
@@ -306,7 +333,7 @@ __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *
     }
     // 2. barrier (failure injection: one arrival too many at the barrier that
     //    covers the step a.stall_step)
-    const bool stall = a.stall_step >= 0 && j >= a.stall_step - 1;
+    const bool stall = a.stall_step >= 0 && j + QRCP_MAXP - 1 >= a.stall_step;
     if (!grid_barrier(bar, (unsigned)((nbar + 1) * G + (stall ? 1 : 0)), a.ctl, a.spin_limit)) return;
     // 3. the winner (one key word) | the largest bound and the candidates above it
     if (tid == 0) {
@@ -400,6 +427,7 @@ __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *
       s_tau = tau;
       s_beta = beta;
       s_scal = (tau != 0.f) ? 1.f / (alpha - beta) : 0.f;
+      s_tl[0] = tau;
       if (b == 0) a.piv[j] = wi;
       a.sel[wi] = 1;
       s_pair = -1;
@@ -410,127 +438,173 @@ __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *
     if (tid < a.s_pad) v[tid] = (tid < j || tid >= s) ? 0.f : ((tid == j) ? 1.f : xt * s_scal);
     if (b == wb && tid == 0) nrm[wi - c0] = -1.f;  // selected
     __syncthreads();
-    // 5. a second pivot: the candidates above every bound, updated by H_j
+    // 5. further pivots: the candidates above every bound, updated by the
+    //    barrier's reflectors so far; the best is certified if it still
+    //    exceeds every bound (see the file comment)
+    int np = 1;  // pivots of this barrier
     if (try_pair) {
-      // the warp's (up to) three candidates side by side, so their
-      // reductions interleave
-      float d[QRCP_CPW], acc[QRCP_CPW];
       bool live[QRCP_CPW];
 #pragma unroll
       for (int r = 0; r < QRCP_CPW; ++r) {
         const int q = wid + 16 * r;
         live[r] = q < ncand && s_cidx[q] != wi;
-        d[r] = 0.f;
-        if (live[r])
-#pragma unroll
-          for (int u = 0; u < QRCP_COL; ++u) {
-            const int t = lane + 32 * u;
-            d[r] = fmaf((t < a.s_pad) ? v[t] : 0.f, xc[r][u], d[r]);
-          }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int r = 0; r < QRCP_CPW; ++r) d[r] += __shfl_xor_sync(0xffffffffu, d[r], o);
-#pragma unroll
-      for (int r = 0; r < QRCP_CPW; ++r) {
-        acc[r] = 0.f;
-        if (live[r]) {
-          float *y = ybuf + (size_t)(wid + 16 * r) * a.s_pad;
-          const float dr = d[r] * tau;
-#pragma unroll
-          for (int u = 0; u < QRCP_COL; ++u) {
-            const int t = lane + 32 * u;
-            if (t < a.s_pad) {
-              const float yt = fmaf(-dr, v[t], xc[r][u]);
-              y[t] = yt;
-              if (t > j) acc[r] = fmaf(yt, yt, acc[r]);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int r = 0; r < QRCP_CPW; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-      if (lane == 0)
+      for (int p = 1; p < QRCP_MAXP && j + p < a.k; ++p) {
+        // candidates <- H_{j+p-1} candidates (kept in registers and in ybuf),
+        // their trailing norms over rows > j + p - 1; the warp's (up to)
+        // three candidates side by side, so their reductions interleave
+        const float *vl = vpt(p - 1);
+        const float tl = s_tl[p - 1];
+        const int jl = j + p - 1;
+        float d[QRCP_CPW], acc[QRCP_CPW];
 #pragma unroll
         for (int r = 0; r < QRCP_CPW; ++r) {
-          const int q = wid + 16 * r;
-          if (q < ncand) s_cnn[q] = live[r] ? acc[r] : -1.f;
+          d[r] = 0.f;
+          if (live[r])
+#pragma unroll
+            for (int u = 0; u < QRCP_COL; ++u) {
+              const int t = lane + 32 * u;
+              d[r] = fmaf((t < a.s_pad) ? vl[t] : 0.f, xc[r][u], d[r]);
+            }
         }
-      __syncthreads();
-      if (wid == 0) {
-        // the best updated norm (ties to the lowest column index), one warp
-        float bn = -1.f;
-        int bq = -1, bidx = 0x7fffffff;
-        for (int q = lane; q < ncand; q += 32) {
-          const float nn = s_cnn[q];
-          const int ci = s_cidx[q];
-          if (nn >= 0.f && (nn > bn || (nn == bn && ci < bidx))) {
-            bn = nn;
-            bq = q;
-            bidx = ci;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int r = 0; r < QRCP_CPW; ++r) d[r] += __shfl_xor_sync(0xffffffffu, d[r], o);
+#pragma unroll
+        for (int r = 0; r < QRCP_CPW; ++r) {
+          acc[r] = 0.f;
+          if (live[r]) {
+            float *y = ybuf + (size_t)(wid + 16 * r) * a.s_pad;
+            const float dr = d[r] * tl;
+#pragma unroll
+            for (int u = 0; u < QRCP_COL; ++u) {
+              const int t = lane + 32 * u;
+              if (t < a.s_pad) {
+                const float yt = fmaf(-dr, vl[t], xc[r][u]);
+                xc[r][u] = yt;
+                y[t] = yt;
+                if (t > jl) acc[r] = fmaf(yt, yt, acc[r]);
+              }
+            }
           }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float on = __shfl_xor_sync(0xffffffffu, bn, o);
-          const int oq = __shfl_xor_sync(0xffffffffu, bq, o), oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-          if (on > bn || (on == bn && oi < bidx)) {
-            bn = on;
-            bq = oq;
-            bidx = oi;
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int r = 0; r < QRCP_CPW; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        if (lane == 0)
+#pragma unroll
+          for (int r = 0; r < QRCP_CPW; ++r) {
+            const int q = wid + 16 * r;
+            if (q < ncand) s_cnn[q] = live[r] ? acc[r] : -1.f;
           }
-        }
-        if (lane == 0) {
-          // certified: strictly above every bound (so above every column not
-          // evaluated, whose norms only shrink under H_j), and not zero
-          if (bq >= 0 && bn > s_bound && bn > 0.f) {
-            const float *y = ybuf + (size_t)bq * a.s_pad;
-            const float alpha2 = y[j + 1];
-            float tau2 = 0.f, beta2 = alpha2;
-            if (bn - alpha2 * alpha2 > 0.f) {
-              const float nx = sqrtf(bn);
-              beta2 = (alpha2 >= 0.f) ? -nx : nx;
-              tau2 = (beta2 - alpha2) / beta2;
+        __syncthreads();
+        if (wid == 0) {
+          // the best updated norm (ties to the lowest column index), one warp
+          float bn = -1.f;
+          int bq = -1, bidx = 0x7fffffff;
+          for (int q = lane; q < ncand; q += 32) {
+            const float nn = s_cnn[q];
+            const int ci = s_cidx[q];
+            if (nn >= 0.f && (nn > bn || (nn == bn && ci < bidx))) {
+              bn = nn;
+              bq = q;
+              bidx = ci;
             }
-            s_tau2 = tau2;
-            s_beta = beta2;
-            s_scal = (tau2 != 0.f) ? 1.f / (alpha2 - beta2) : 0.f;
-            s_pair = bq;
-            s_win_col = bidx;
-            if (b == 0) a.piv[j + 1] = bidx;
-            a.sel[bidx] = 1;
           }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float on = __shfl_xor_sync(0xffffffffu, bn, o);
+            const int oq = __shfl_xor_sync(0xffffffffu, bq, o), oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            if (on > bn || (on == bn && oi < bidx)) {
+              bn = on;
+              bq = oq;
+              bidx = oi;
+            }
+          }
+          if (lane == 0) {
+            s_pair = -1;
+            // certified: strictly above every bound (so above every column not
+            // evaluated, whose norms only shrink under the reflectors), and
+            // not zero
+            if (bq >= 0 && bn > s_bound && bn > 0.f) {
+              const float *y = ybuf + (size_t)bq * a.s_pad;
+              const float alpha2 = y[j + p];
+              float tau2 = 0.f, beta2 = alpha2;
+              if (bn - alpha2 * alpha2 > 0.f) {
+                const float nx = sqrtf(bn);
+                beta2 = (alpha2 >= 0.f) ? -nx : nx;
+                tau2 = (beta2 - alpha2) / beta2;
+              }
+              s_tl[p] = tau2;
+              s_beta = beta2;
+              s_scal = (tau2 != 0.f) ? 1.f / (alpha2 - beta2) : 0.f;
+              s_pair = bq;
+              s_win_col = bidx;
+              if (b == 0) a.piv[j + p] = bidx;
+              a.sel[bidx] = 1;
+            }
+          }
+        }
+        __syncthreads();
+        const int pq = s_pair;
+        if (pq < 0) break;  // uniform: every block takes the same decision
+        {
+          const float *y = ybuf + (size_t)pq * a.s_pad;
+          const int ci = s_win_col;
+          const float yt = (tid < a.s_pad) ? y[tid] : 0.f;
+          if (b == 0 && tid < a.k)
+            a.S11[(size_t)tid * a.k + j + p] = (tid < j + p) ? yt : ((tid == j + p) ? s_beta : 0.f);
+          if (tid < a.s_pad) vpt(p)[tid] = (tid < j + p || tid >= s) ? 0.f : ((tid == j + p) ? 1.f : yt * s_scal);
+          if (ci >= c0 && ci < c0 + ncol && tid == 0) nrm[ci - c0] = -1.f;
+#pragma unroll
+          for (int r = 0; r < QRCP_CPW; ++r)
+            if (wid + 16 * r == pq) live[r] = false;
+        }
+        ++np;
+        __syncthreads();
+      }
+    }
+    if (np > 1) {
+      // the Gram entries v_i.v_l (l < i) of the barrier's reflectors, one warp each
+      constexpr int NPAIR = QRCP_MAXP * (QRCP_MAXP - 1) / 2;
+      if (wid < NPAIR) {
+        int ii = 1, ll = wid;
+        while (ll >= ii) {
+          ll -= ii;
+          ++ii;
+        }
+        if (ii < np) {
+          float c = 0.f;
+          const float *vi = vpt(ii), *vl = vpt(ll);
+          for (int t = lane; t < a.s_pad; t += 32) c = fmaf(vi[t], vl[t], c);
+          c = warp_sum(c);
+          if (lane == 0) s_cc[ii][ll] = c;
         }
       }
       __syncthreads();
-    }
-    const int pq = s_pair;
-    if (pq >= 0) {
-      const float *y = ybuf + (size_t)pq * a.s_pad;
-      const int ci = s_win_col;
-      const float yt = (tid < a.s_pad) ? y[tid] : 0.f;
-      if (b == 0 && tid < a.k) a.S11[(size_t)tid * a.k + j + 1] = (tid <= j) ? yt : ((tid == j + 1) ? s_beta : 0.f);
-      if (tid < a.s_pad) v2[tid] = (tid <= j || tid >= s) ? 0.f : ((tid == j + 1) ? 1.f : yt * s_scal);
-      if (ci >= c0 && ci < c0 + ncol && tid == 0) nrm[ci - c0] = -1.f;
-      __syncthreads();
-      if (wid == 0) {  // v2 . v
-        float c = 0.f;
-        for (int t = lane; t < a.s_pad; t += 32) c = fmaf(v2[t], v[t], c);
-        c = warp_sum(c);
-        if (lane == 0) s_c12 = c;
+      float *vps[QRCP_MAXP];
+#pragma unroll
+      for (int i = 0; i < QRCP_MAXP; ++i) vps[i] = vpt(i);
+      switch (np) {
+        case 2:
+          apply_reflectors_lanes<2, 2>(slab, a.s_pad, ncol, vps, s_tl, s_cc, j, nrm);
+          break;
+        case 3:
+          apply_reflectors_lanes<3, 2>(slab, a.s_pad, ncol, vps, s_tl, s_cc, j, nrm);
+          break;
+        default:
+          apply_reflectors_lanes<QRCP_MAXP, 2>(slab, a.s_pad, ncol, vps, s_tl, s_cc, j, nrm);
+          break;
       }
-      __syncthreads();
-      apply_two_reflectors_lanes<2>(slab, a.s_pad, ncol, v, tau, v2, s_tau2, s_c12, j, nrm);
-      j += 2;
     } else {
       apply_reflector_lanes<float, 2>(slab, a.s_pad, ncol, v, tau, j, nrm);
-      j += 1;
     }
+    j += np;
     __syncthreads();
   }
+  if (b == 0 && tid == 0) a.ctl[CTL_QRCP_BARRIERS] = nbar;
 }
 
 template <typename T>
@@ -565,9 +639,9 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
   }
   __syncthreads();
   if constexpr (sizeof(T) == 4) {
-    float *v2 = reinterpret_cast<float *>(nrm + a.cols_per_block);
-    v2 = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(v2) + 15) & ~(uintptr_t)15);
-    qrcp_pairs_f32(a, slab, v, nrm, v2, v2 + a.s_pad, c0, ncol);
+    float *vx = reinterpret_cast<float *>(nrm + a.cols_per_block);
+    vx = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(vx) + 15) & ~(uintptr_t)15);
+    qrcp_pairs_f32(a, slab, v, nrm, vx, c0, ncol);
   } else {
 
     for (int j = 0; j < a.k; ++j) {

@@ -94,6 +94,8 @@ def test_mixed_graded_matches_oracle(shape, k, p, ratio, mode):
     # each second Cholesky-QR sweep takes the first-order expansion
     ctl = got["ctl"]
     assert ctl[14] == 3 and ctl[15] == 0, ctl[13:16]
+    # the QRCP certifies up to four pivots per grid barrier (word 38 counts them)
+    assert -(-k // 4) <= ctl[38] < k, ctl[38]
 
 
 @pytest.mark.parametrize("mode", [ffsrqr.MIXED_TF32X3, ffsrqr.MIXED_BF16X3])
