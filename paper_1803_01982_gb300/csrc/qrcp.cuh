@@ -32,7 +32,7 @@
 // reflectors are then applied to the slabs in one pass.  Every block computes
 // the same certificates from the same published data, so all take the same
 // decisions.  On the benchmark sketch (k = 200) the barriers fall from 108
-// (at most two pivots each) to about 70.
+// (at most two pivots each) to 68.
 // Outputs: piv[0:k] (original indices, in pivot order), S11 (k x k, row-major,
 // the R factor of the pivoted sketch columns: S11(0:j, j) = transformed pivot
 // column above the diagonal, S11(j, j) = beta), status RANK_DEFICIENT if a
@@ -271,13 +271,13 @@ __device__ __forceinline__ void block_top2(float &v1, int &i1, float &v2, float 
   __syncthreads();
 }
 
-// Single precision: up to two pivots per grid barrier (see the file comment).
+// Single precision: up to QRCP_MAXP pivots per grid barrier (see the file comment).
 // After the barrier only two dependent L2 round trips sit on the critical
 // path: (winner key | candidate table), then (winner column | candidate
 // columns, prefetched by the candidate warps into registers).
 constexpr int QRCP_TAB = 8;   // candidate-table entries per lane (grid <= 256)
 constexpr int QRCP_COL = 8;   // column entries per lane (s_pad <= 256)
-__device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *slab, float *v, float *nrm,
+__device__ __forceinline__ void qrcp_multi_f32(const QrcpArgs<float> &a, float *slab, float *v, float *nrm,
                                                float *vx, int64_t c0, int ncol) {
   // reflector i of a barrier: v (the winner's), then the QRCP_MAXP - 1 vectors
   // at vx; the candidate columns after them
@@ -396,7 +396,7 @@ __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *
       ++j;
       continue;
     }
-    const bool try_pair = j + 1 < a.k && ncand <= QRCP_MAXC && s_wv > 0.f;
+    const bool try_more = j + 1 < a.k && ncand <= QRCP_MAXC && s_wv > 0.f;
     // 4. winner column | candidate columns (warp w holds candidates w, w + 16,
     //    w + 32 in registers)
     const float *x = a.cand_col + ((size_t)buf * G + wb) * a.lds;
@@ -405,7 +405,7 @@ __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *
 #pragma unroll
     for (int r = 0; r < QRCP_CPW; ++r) {
       const int q = wid + 16 * r;
-      if (try_pair && q < ncand && s_cidx[q] != wi) {
+      if (try_more && q < ncand && s_cidx[q] != wi) {
         const float *src = a.cand_col + ((size_t)buf * G + s_cblk[q]) * a.lds;
 #pragma unroll
         for (int u = 0; u < QRCP_COL; ++u) {
@@ -442,7 +442,7 @@ __device__ __forceinline__ void qrcp_pairs_f32(const QrcpArgs<float> &a, float *
     //    barrier's reflectors so far; the best is certified if it still
     //    exceeds every bound (see the file comment)
     int np = 1;  // pivots of this barrier
-    if (try_pair) {
+    if (try_more) {
       bool live[QRCP_CPW];
 #pragma unroll
       for (int r = 0; r < QRCP_CPW; ++r) {
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs<T> a) {
   if constexpr (sizeof(T) == 4) {
     float *vx = reinterpret_cast<float *>(nrm + a.cols_per_block);
     vx = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(vx) + 15) & ~(uintptr_t)15);
-    qrcp_pairs_f32(a, slab, v, nrm, vx, c0, ncol);
+    qrcp_multi_f32(a, slab, v, nrm, vx, c0, ncol);
   } else {
 
     for (int j = 0; j < a.k; ++j) {
