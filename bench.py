@@ -263,6 +263,35 @@ def max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def gpu_local_cpus(index: int):
+    """The CPUs of the host memory node that sysfs lists for GPU `index` (via
+    nvidia-smi's PCI bus id), or None when that is not known."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i", str(index)],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        if not bus:
+            return None
+        dom, rest = bus.split(":", 1)
+        dev = f"{int(dom, 16):04x}:{rest}"
+        with open(f"/sys/bus/pci/devices/{dev}/numa_node") as f:
+            node = int(f.read().strip())
+        if node < 0:
+            return None
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return None
+
+
 def replica_seed(rank: int) -> int:
     """Each replica factors its own matrix of the same recipe."""
     return 1 + rank
@@ -335,9 +364,20 @@ def run_ours(a, rank, world, local_rank):
     # computation) and each step's U, S, V, piv back to pinned host memory
     e2e = None
     if a.e2e_steps > 0:
-        Ah = A.cpu().pin_memory()
-        pipe = ffsrqr.Pipe(plan)
-        host_out = [pipe.host_outputs() for _ in range(2)]
+        # the pinned host buffers are placed on the GPU's own host memory node
+        # when sysfs names one (the allocating thread's CPUs decide where the
+        # pages go); the affinity is restored afterwards
+        local = gpu_local_cpus(local_rank)
+        saved = os.sched_getaffinity(0) if local else None
+        if local:
+            os.sched_setaffinity(0, local)
+        try:
+            Ah = A.cpu().pin_memory()
+            pipe = ffsrqr.Pipe(plan)
+            host_out = [pipe.host_outputs() for _ in range(2)]
+        finally:
+            if saved:
+                os.sched_setaffinity(0, saved)
         pipe.run([Ah], [host_out[0]], stream=st)  # warm-up
         torch.cuda.synchronize(dev)
         if world > 1:
@@ -350,7 +390,9 @@ def run_ours(a, rank, world, local_rank):
         ems = max_over_ranks(e0.elapsed_time(e1) / a.e2e_steps, dev)
         d2h = sum(t.numel() * t.element_size() for t in out)
         e2e = {"value": world * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": A.numel() * 4,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+               "d2h_bytes_per_step": d2h, "ms_per_step": ems,
+               "host_buffers": (f"pinned on the GPU's node (CPUs {min(local)}-{max(local)})" if local
+                                else "pinned, node not pinned (sysfs names none)")}
 
     # the three arithmetic modes on the same matrix (a few steps each) and
     # their errors against the FP64 oracle run on the same array, which is
