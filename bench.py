@@ -263,6 +263,19 @@ def max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def parse_cpulist(text: str) -> set:
+    """The CPUs of a sysfs cpulist such as "0-7,16,18-19"."""
+    cpus = set()
+    for part in text.strip().split(","):
+        part = part.strip()
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
 def gpu_local_cpus(index: int):
     """The CPUs of the host memory node that sysfs lists for GPU `index` (via
     nvidia-smi's PCI bus id), or None when that is not known."""
@@ -278,15 +291,7 @@ def gpu_local_cpus(index: int):
         if node < 0:
             return None
         with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
-            text = f.read().strip()
-        cpus = set()
-        for part in text.split(","):
-            if "-" in part:
-                lo, hi = part.split("-")
-                cpus.update(range(int(lo), int(hi) + 1))
-            elif part:
-                cpus.add(int(part))
-        cpus &= os.sched_getaffinity(0)
+            cpus = parse_cpulist(f.read()) & os.sched_getaffinity(0)
         return cpus or None
     except (OSError, ValueError, subprocess.SubprocessError):
         return None

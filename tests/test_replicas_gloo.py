@@ -70,3 +70,13 @@ def test_missing_rank_is_detected_by_timeout(tmp_path):
     while not ctx.join(timeout=60):
         pass
     assert open(tmp_path / "r0.txt").read().startswith("timeout")
+
+
+def test_cpulist_parsing():
+    # the host memory node's CPU list the e2e measurement binds its pinned
+    # buffers to (sysfs format)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_cpulist("0-15\n") == set(range(16))
+    assert bench.parse_cpulist("0-3,8,10-11") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("") == set()
