@@ -115,3 +115,27 @@ def test_blocked_plan_argument_checks():
     assert f(ctypes.byref(h), 200, 150, 40, 16, 8, 0, None, None) == -9
     assert f(ctypes.byref(h), 200, 150, 40, 16, 8, 0, None, ctypes.byref(ws)) == 0
     assert lib.ffsrqr_destroy(h) == 0
+
+
+@pytest.mark.parametrize("b", [8])
+def test_blocked_exact_and_deficient_rank(b):
+    # exactly rank k (a ragged last block of 4): the singular values are the
+    # true ones; rank 5 < k = 16: the second block's sample is rounding noise,
+    # its columns are orthogonalised against the first block's anyway, and
+    # the approximation still holds the whole range
+    import math
+    B = synth.rank_k(256, 200, 12, seed=10).astype(np.float32)
+    got = run(B, 12, b, 6, ffsrqr.PLAIN_FP32, seed=1)
+    sv = np.linalg.svd(B.astype(np.float64), compute_uv=False)
+    np.testing.assert_allclose(got["S"], sv[:12], rtol=2e-5)
+    res = np.linalg.norm(B - (got["U"] * got["S"]) @ got["V"].T)
+    assert res <= 1e-5 * sv[0] * math.sqrt(256 * 200)
+    C = synth.rank_k(300, 240, 5, seed=12).astype(np.float32)
+    got = run(C, 16, b, 6, ffsrqr.PLAIN_FP32, seed=2)
+    sv = np.linalg.svd(C.astype(np.float64), compute_uv=False)
+    assert got["info"]["status"] in (0, 1)
+    np.testing.assert_allclose(got["S"][:5], sv[:5], rtol=2e-5)
+    assert np.all(got["S"][5:] <= 2e-5 * sv[0])  # FP32 noise (measured 4.4e-6)
+    res = np.linalg.norm(C - (got["U"] * got["S"]) @ got["V"].T)
+    assert res <= 1e-5 * sv[0] * math.sqrt(300 * 240)
+    assert np.allclose(got["U"][:, :5].T @ got["U"][:, :5], np.eye(5), atol=1e-4)

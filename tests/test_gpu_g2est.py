@@ -110,3 +110,19 @@ def test_set_g2_rows_errors():
     rsi = ffsrqr.Plan(64, 48, 8, 4, ffsrqr.PLAIN_FP32, rsi_q=1)
     with pytest.raises(ffsrqr.FfsrqrError, match="returned 7"):
         rsi.set_g2_rows(4)
+
+
+def test_estimate_on_exact_rank():
+    # alpha is rounding noise when A has rank k: the estimate's columns
+    # R11^{-1}(alpha w_top - a w_k) stay finite (no division by alpha), and
+    # whatever swaps the estimate asks for keep the factorisation exact
+    import math
+    B = synth.rank_k(256, 200, 12, seed=10).astype(np.float32)
+    got = run(B, 12, 6, ffsrqr.PLAIN_FP32, 2.0, 4)
+    info = got["info"]
+    assert info["status"] in (0, 2)
+    assert math.isfinite(info["g2_first"]) and math.isfinite(info["g2_final"])
+    sv = np.linalg.svd(B.astype(np.float64), compute_uv=False)
+    np.testing.assert_allclose(got["S"], sv[:12], rtol=2e-5)
+    res = np.linalg.norm(B - (got["U"] * got["S"]) @ got["V"].T)
+    assert res <= 1e-5 * sv[0] * math.sqrt(256 * 200)
