@@ -944,10 +944,16 @@ int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *p
   // a6: R11, R11^{-1}, Z^T = G^T R11^{-T}
   extract_r11_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.gt, ldk, k, piv, w.r11, nullptr);
   CKL("extract_r11");
-  if (P->g2_rows == 0) {  // R11^{-1} for the exact g2 (the estimate solves with R11 itself)
-    eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, st>>>(w.rinv, k, k);
+  const bool fork_rinv = P->g2_rows == 0;  // the estimate solves with R11 itself
+  if (fork_rinv) {
+    // R11^{-1} for the exact g2, on the plan's side stream while Z^T and the
+    // trailing-norm estimate are formed (joined before the g2 kernel)
+    CK(cudaEventRecord(P->ev_fork, st));
+    CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    eye_kernel<T><<<(unsigned)cdiv((int64_t)k * k, 256), 256, 0, P->side>>>(w.rinv, k, k);
     CKL("eye");
-    if ((rc = launch_trsm<T, true>(st, P, w.rinv, k, k, w.r11, k, 1))) return rc;
+    if ((rc = launch_trsm<T, true>(P->side, P, w.rinv, k, k, w.r11, k, 1))) return rc;
+    CK(cudaEventRecord(P->ev_join, P->side));
   }
   copy2d_kernel<T><<<(unsigned)std::min<int64_t>(cdiv(n * k, 256), 8 * nsm), 256, 0, st>>>(w.gt, ldk, w.zt,
                                                                                           ldk, n, k, nullptr);
@@ -966,6 +972,7 @@ int run_pre(ffsrqr_plan_s *P, const T *A, int64_t lda, uint64_t seed, int32_t *p
   }
   trailing_norms_kernel<T><<<P->nblk_tn, 256, 0, st>>>(w.bt, w.cbt, lds, n, s, w.sel, w.r, w.bv, w.bi);
   CKL("trailing_norms");
+  if (fork_rinv) CK(cudaStreamWaitEvent(st, P->ev_join, 0));
   if (k < n) {
     if ((rc = srqr_test<T>(st, P, w, A, lda, seed, 1))) return rc;
   }
