@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--mode", choices=["mixed", "bf16x3", "plain"], default="bf16x3",
                     help="mixed: TF32 sketch and three-product TF32 passes; bf16x3: BF16 sketch and "
                          "three-product split-BF16 passes; plain: FP32 on the CUDA cores")
-    ap.add_argument("--decay", choices=["slow", "fast"], default="slow")
+    ap.add_argument("--decay", choices=["slow", "fast", "geo95"], default="slow",
+                    help="sigma_j = j^-1.5 (slow), 0.97^j (fast) or 0.95^j (geo95, the 50000x8000 case)")
     ap.add_argument("--m", type=int, default=20000)
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--k", type=int, default=200)
@@ -74,13 +75,15 @@ def parse():
 
 
 def workload_name(a):
-    d = "sigma_j=j^-1.5" if a.decay == "slow" else "sigma_j=0.97^j"
+    d = {"slow": "sigma_j=j^-1.5", "fast": "sigma_j=0.97^j", "geo95": "sigma_j=0.95^j"}[a.decay]
     return f"FFSRQR rank-{a.k} of {a.m}x{a.n} FP32, r=2000, {d}, E~N(0,1e-6^2)"
 
 
 def spectrum(a, r):
     from paper_1803_01982_gb300 import synth
-    return synth.slow_decay(r) if a.decay == "slow" else synth.fast_decay(r)
+    if a.decay == "slow":
+        return synth.slow_decay(r)
+    return synth.fast_decay(r, 0.97 if a.decay == "fast" else 0.95)
 
 
 # --------------------------------------------------------------------------
